@@ -1,0 +1,220 @@
+/*
+ * pcgipm.h -- C ABI of the GB300 preconditioned inexact interior-point QP solver.
+ *
+ * Method: Karim & Solomonik, "Efficient Preconditioners for Interior Point
+ * Methods via a new Schur Complement-Based Strategy".  The QP (Sec. 1,
+ * eq. [qp]) is
+ *
+ *     minimise 1/2 x'Hx + c'x   subject to   A x = b,   C x >= d,
+ *
+ * H (n x n) symmetric positive definite, A (m1 x n) of full row rank, C (m2 x n).
+ * The hot path is the preconditioned CG solve of the inequality-constraint
+ * reduced system K_F dnu = r_nu (Sec. 4.1, eq. [ineq-const-reduced]) with
+ *
+ *     K_F = D + [C 0] K0^{-1} [C'; 0],   K0 = [H A'; A 0],   D = V^{-1} S,
+ *
+ * which is the paper's D - [C 0] F^{-1} [C'; 0] with F = [-H A'; A 0] = -J K0 J,
+ * J = diag(-I_n, I_m1).  K0 is factored once per QP (the setup phase of Sec. 4.1)
+ * and reused at every IPM iteration; K_F is never formed (Sec. 5.2: a product
+ * with C', a solve with the K0 factor, a product with C).
+ *
+ * Conventions for every call below
+ * --------------------------------
+ * - Dense matrices are row-major FP64 with leading dimension equal to their
+ *   column count; vectors are FP64.
+ * - ptr_kind = QP_PTR_HOST: pointers are host memory (pageable or pinned);
+ *   the call copies in/out and returns after the results are in place.
+ *   ptr_kind = QP_PTR_DEVICE: pointers are device memory of the current CUDA
+ *   device; the call is ordered on the solver's stream and returns after the
+ *   results are written (it synchronises that stream).
+ * - Inputs are copied; the caller keeps ownership of every buffer it passes.
+ *   Outputs are written into caller-owned buffers.
+ * - All device work runs on opts.stream (a cudaStream_t cast to void*), or on
+ *   a stream the library creates when it is NULL.
+ * - Every call returns QP_OK (0) or a negative status from the enum below;
+ *   qp_strerror gives its text.  A call that fails leaves the handle usable
+ *   unless it returned QP_ECUDA (a CUDA runtime error; the handle should be
+ *   destroyed).
+ */
+#ifndef PCGIPM_H
+#define PCGIPM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum qp_status {
+    QP_OK = 0,
+    QP_EINVAL = -1,       /* bad dimension, NULL pointer, NaN/Inf input, asymmetric H */
+    QP_ENOMEM = -2,       /* device allocation failed */
+    QP_ESINGULAR = -3,    /* A H^{-1} A' has a non-positive pivot: A rank-deficient (Sec. 1 assumes full rank) */
+    QP_ENOTCONVEX = -4,   /* H has a non-positive pivot: not positive definite (Sec. 1 assumption) */
+    QP_EMAXIT = -5,       /* IPM iteration limit reached without meeting the tolerances */
+    QP_ENUMERIC = -6,     /* NaN/Inf appeared during the iteration */
+    QP_ETIMEOUT = -7,     /* a bounded device-side wait expired */
+    QP_EAGAIN = -8,       /* result not ready yet */
+    QP_ECUDA = -9,        /* CUDA runtime error */
+    QP_ESTATE = -10       /* call out of order (e.g. solve before qp_factor_K0) */
+};
+
+enum qp_precision {
+    QP_PREC_FP64 = 0,     /* factor, C copies and PCG all in FP64 */
+    QP_PREC_FP32 = 1      /* mixed: P_H factor in FP32; C copies, K0 factor and PCG in FP32 until
+                             FP64 refinement contracts by less than 4x per sweep, then in FP64
+                             (a second, FP64 factor of K0); FP64 residuals, refinement, step logic */
+};
+
+enum qp_precond {
+    QP_PC_AUTO = 0,       /* P_L if m1 >= n/2 else P_H (Corollaries 1 and 2: n-m1+1 vs m1+1 iterations) */
+    QP_PC_PL = 1,         /* P_L = D, Sec. 4.2 eq. [preconditioner-1] */
+    QP_PC_PH_EXACT = 2,   /* P_H = D + C H^{-1} C', Sec. 4.2 eq. [preconditioner-2] */
+    QP_PC_PH_DIAG = 3,    /* P_H with diag(H)^{-1}, the variant of the experiments (Sec. 5.2, PH-KF) */
+    QP_PC_NONE = 4        /* unpreconditioned CG on K_F (the U-KF variant of Sec. 6) */
+};
+
+enum qp_pcg_mode {
+    QP_MODE_PARITY = 0,   /* each Newton direction refined against its FP64 residual */
+    QP_MODE_PAPER = 1     /* one PCG solve per direction at the paper's eps = 1e-3, no refinement (Sec. 6) */
+};
+
+enum qp_ptr_kind { QP_PTR_HOST = 0, QP_PTR_DEVICE = 1 };
+
+typedef struct qp_s *qp_t;   /* opaque; owns every device buffer it allocates */
+
+typedef struct {
+    int precision;        /* enum qp_precision */
+    int precond;          /* enum qp_precond */
+    int pcg_mode;         /* enum qp_pcg_mode */
+    int max_ipm;          /* IPM iteration limit (default 100) */
+    int max_pcg;          /* PCG iteration limit per solve (default 4 * m2 + 50) */
+    int refine_max;       /* refinement sweeps per Newton direction after the first solve (default 5) */
+    double pcg_tol;       /* PCG relative residual tolerance; <= 0 selects the mode's default */
+    double refine_tol;    /* stop refining when |rho|_2 <= refine_tol |rhs|_2 (default 1e-11) */
+    double tol_feas;      /* scaled primal/dual infeasibility tolerance (default 1e-10) */
+    double tol_mu;        /* stop when mu <= tol_mu (1 + |f|) (default 1e-11) */
+    int pcg_check_every;  /* PCG iterations per convergence check (default 8) */
+    void *stream;         /* cudaStream_t, or NULL for a library-created stream */
+} qp_opts;
+
+typedef struct {
+    int status;           /* last status of qp_ipm_solve */
+    int precond_used;     /* resolved enum qp_precond */
+    int ipm_iters;
+    long long pcg_iters_total;
+    int newton_solves;    /* reduced solves (predictor + corrector + refinement corrections) */
+    int refine_sweeps;    /* total refinement corrections */
+    double res_p, res_d, mu, obj;   /* final scaled residuals, mu, objective */
+    double t_factor_ms;   /* device time of qp_factor_K0 */
+    double t_solve_ms;    /* wall time of the last qp_ipm_solve */
+    double t_pcg_ms;      /* device time spent in PCG iterations during the last solve */
+    double t_precond_ms;  /* device time of the per-iteration P_H factorizations */
+    int op64_solves;      /* QP_PREC_FP32: reduced solves run with the FP64 operator after a switch */
+    int op64_switch_iter; /* QP_PREC_FP32: IPM iteration of the switch to the FP64 operator, or -1 */
+} qp_stats;
+
+/* Fill *opts with the defaults listed in the struct comments. */
+void qp_opts_default(qp_opts *opts);
+
+/*
+ * Create a QP handle from the problem data of Sec. 1, eq. [qp]:
+ * H (n x n, symmetric), c (n), A (m1 x n, m1 may be 0 with A = b = NULL),
+ * b (m1), C (m2 x n, dense), d (m2).  Requires 1 <= n, 0 <= m1 <= n, 1 <= m2.
+ * Copies everything to the device; validates symmetry of H (relative 1e-12)
+ * and finiteness (QP_EINVAL).  opts may be NULL (defaults).
+ */
+int qp_create(qp_t *out, int n, int m1, int m2,
+              const double *H, const double *c, const double *A, const double *b,
+              const double *C, const double *d, const qp_opts *opts, int ptr_kind);
+
+/*
+ * Setup phase (Sec. 4.1: F is factored once per QP, before the IPM iterations).
+ * Factors K0 = [H A'; A 0] = L diag(I_n, -I_m1) L' with L = [R' 0; G L_S],
+ * H = R'R, G = A R^{-1}, A H^{-1} A' = L_S L_S' (the inertia of Sec. 4.1:
+ * n pivots of H and m1 of F_H, all checked positive in FP64).  The triangular
+ * factors are stored inverted (R^{-T}, L_S^{-1} G, L_S^{-1}) in the working
+ * precision so that each triangular solve is a parallel triangular
+ * matrix-vector product.  For P_H it also forms T = C H^{-1} C' (or
+ * C diag(H)^{-1} C').  Idempotent.  Returns QP_ENOTCONVEX / QP_ESINGULAR on a
+ * non-positive pivot.
+ */
+int qp_factor_K0(qp_t qp);
+
+/*
+ * One product q = K_F p with the implicit K_F (Sec. 5.2, three steps) for a
+ * caller-given positive diagonal D (m2).  D, p, q: m2 vectors.  Runs in the
+ * handle's working precision.  Needs qp_factor_K0.
+ */
+int qp_kf_apply(qp_t qp, const double *D, const double *p, double *q, int ptr_kind);
+
+/*
+ * Solve K0 [a; b] = [u; w] with the stored factor (forward solve, D^{-1},
+ * back solve of the LDL' factor; Sec. 4.1 setup/solve split).  u, a: n;
+ * w, b: m1 (w may be NULL for zero; b may be NULL if not wanted).
+ */
+int qp_k0_solve(qp_t qp, const double *u, const double *w, double *a, double *b, int ptr_kind);
+
+/*
+ * The hot path by itself: preconditioned CG on K_F dnu = rhs (Sec. 4.1,
+ * eq. [ineq-const-reduced]) from a zero start, stopping when
+ * |r|_2 <= tol |rhs|_2 or after maxit iterations (Sec. 6 settings).
+ * D (m2, positive) parameterises K_F and P_L / P_H as in Theorems 1 and 2.
+ * precond: enum qp_precond (AUTO resolves as in qp_opts).  iters / relres may
+ * be NULL.  Returns QP_EMAXIT if maxit was reached before tol (dnu still holds
+ * the last iterate).
+ */
+int qp_pcg_reduced_solve(qp_t qp, const double *D, const double *rhs, double *dnu,
+                         int precond, double tol, int maxit, int *iters, double *relres,
+                         int ptr_kind);
+
+/*
+ * Full primal-dual IPM (Sec. 2) whose Newton directions come from the reduced
+ * system: per iteration FP64 residuals (eq. [rhs-KKT4]), D = V^{-1} S,
+ * [P_H: refactor D + T], Mehrotra predictor and corrector each solved by
+ * r_nu -> PCG -> recovery (eq. [schur-delta-x]) -> ds (eq. [delz]) and, in
+ * PARITY mode, refined against the FP64 residual of the 3x3 system
+ * (eq. [augmented]); one step length with fraction-to-boundary 0.995.
+ * Outputs x (n), lam (m1), nu (m2), s (m2) may be NULL individually; obj,
+ * ipm_iters, pcg_iters_total may be NULL.  Runs qp_factor_K0 first if needed.
+ */
+int qp_ipm_solve(qp_t qp, double *x, double *lam, double *nu, double *s,
+                 double *obj, int *ipm_iters, long long *pcg_iters_total, int ptr_kind);
+
+/* Copy the handle's counters and timings into *st. */
+int qp_get_stats(qp_t qp, qp_stats *st);
+
+/* Bytes of device memory the handle holds (after qp_factor_K0: its peak). */
+size_t qp_device_bytes(qp_t qp);
+
+/*
+ * Per-PCG-iteration algorithmic traffic of the handle's hot path in bytes,
+ * for a given preconditioner: 2 m2 n (C' and C) + the triangles of the
+ * stored K0 factor + [P_H] m2^2 + the vector traffic, times the element size.
+ */
+double qp_pcg_bytes_per_iter(qp_t qp, int precond);
+
+/*
+ * Time the hot path: run `iters` PCG iterations (no early stop) on K_F with
+ * diagonal D (device or host per ptr_kind) after `warmup` untimed ones and
+ * return the mean device time of one iteration in *ms_per_iter (CUDA events
+ * on the solver stream).  Needs qp_factor_K0.
+ */
+int qp_time_pcg_iteration(qp_t qp, const double *D, int precond, int warmup, int iters,
+                          double *ms_per_iter, int ptr_kind);
+
+/*
+ * Number of this library's kernel launches that have reached the current
+ * device since it was loaded (each kernel counts itself once; graph-launched
+ * kernels included).  Synchronises the device.  Returns 0 on a CUDA error.
+ */
+unsigned long long qp_kernel_launches(void);
+
+void qp_destroy(qp_t qp);
+const char *qp_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PCGIPM_H */

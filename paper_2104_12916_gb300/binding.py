@@ -1,0 +1,254 @@
+"""ctypes binding of libpcgipm.so: the C ABI of include/pcgipm.h with the same names.
+
+Argument marshalling only: every step of the solver runs in the CUDA library.
+Arrays are either host numpy float64 arrays (C-contiguous) or torch CUDA
+float64 tensors (contiguous); the pointer kind is taken from the arrays.
+Loading fails loudly when the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import numpy as np
+
+from . import build as _build
+
+QP_OK, QP_EINVAL, QP_ENOMEM, QP_ESINGULAR, QP_ENOTCONVEX = 0, -1, -2, -3, -4
+QP_EMAXIT, QP_ENUMERIC, QP_ETIMEOUT, QP_EAGAIN, QP_ECUDA, QP_ESTATE = -5, -6, -7, -8, -9, -10
+QP_PREC_FP64, QP_PREC_FP32 = 0, 1
+QP_PC_AUTO, QP_PC_PL, QP_PC_PH_EXACT, QP_PC_PH_DIAG, QP_PC_NONE = 0, 1, 2, 3, 4
+QP_MODE_PARITY, QP_MODE_PAPER = 0, 1
+QP_PTR_HOST, QP_PTR_DEVICE = 0, 1
+
+EXPORTED = [
+    "qp_opts_default", "qp_create", "qp_factor_K0", "qp_kf_apply", "qp_k0_solve",
+    "qp_pcg_reduced_solve", "qp_ipm_solve", "qp_get_stats", "qp_device_bytes",
+    "qp_pcg_bytes_per_iter", "qp_time_pcg_iteration", "qp_kernel_launches", "qp_destroy", "qp_strerror",
+]
+
+
+class qp_opts(ct.Structure):
+    _fields_ = [
+        ("precision", ct.c_int), ("precond", ct.c_int), ("pcg_mode", ct.c_int),
+        ("max_ipm", ct.c_int), ("max_pcg", ct.c_int), ("refine_max", ct.c_int),
+        ("pcg_tol", ct.c_double), ("refine_tol", ct.c_double), ("tol_feas", ct.c_double),
+        ("tol_mu", ct.c_double), ("pcg_check_every", ct.c_int), ("stream", ct.c_void_p),
+    ]
+
+
+class qp_stats(ct.Structure):
+    _fields_ = [
+        ("status", ct.c_int), ("precond_used", ct.c_int), ("ipm_iters", ct.c_int),
+        ("pcg_iters_total", ct.c_longlong), ("newton_solves", ct.c_int), ("refine_sweeps", ct.c_int),
+        ("res_p", ct.c_double), ("res_d", ct.c_double), ("mu", ct.c_double), ("obj", ct.c_double),
+        ("t_factor_ms", ct.c_double), ("t_solve_ms", ct.c_double), ("t_pcg_ms", ct.c_double),
+        ("t_precond_ms", ct.c_double), ("op64_solves", ct.c_int), ("op64_switch_iter", ct.c_int),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load libpcgipm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libpcgipm.so not built at {path}: run paper_2104_12916_gb300.build.build()")
+    lib = ct.CDLL(path)
+    P = ct.c_void_p
+    D = ct.c_double
+    I = ct.c_int
+    lib.qp_opts_default.argtypes = [ct.POINTER(qp_opts)]
+    lib.qp_opts_default.restype = None
+    lib.qp_create.argtypes = [ct.POINTER(P), I, I, I, P, P, P, P, P, P, ct.POINTER(qp_opts), I]
+    lib.qp_factor_K0.argtypes = [P]
+    lib.qp_kf_apply.argtypes = [P, P, P, P, I]
+    lib.qp_k0_solve.argtypes = [P, P, P, P, P, I]
+    lib.qp_pcg_reduced_solve.argtypes = [P, P, P, P, I, D, I, ct.POINTER(I), ct.POINTER(D), I]
+    lib.qp_ipm_solve.argtypes = [P, P, P, P, P, ct.POINTER(D), ct.POINTER(I), ct.POINTER(ct.c_longlong), I]
+    lib.qp_get_stats.argtypes = [P, ct.POINTER(qp_stats)]
+    lib.qp_device_bytes.argtypes = [P]
+    lib.qp_device_bytes.restype = ct.c_size_t
+    lib.qp_pcg_bytes_per_iter.argtypes = [P, I]
+    lib.qp_pcg_bytes_per_iter.restype = D
+    lib.qp_time_pcg_iteration.argtypes = [P, P, I, I, I, ct.POINTER(D), I]
+    lib.qp_kernel_launches.argtypes = []
+    lib.qp_kernel_launches.restype = ct.c_ulonglong
+    lib.qp_destroy.argtypes = [P]
+    lib.qp_destroy.restype = None
+    lib.qp_strerror.argtypes = [I]
+    lib.qp_strerror.restype = ct.c_char_p
+    for name in ("qp_create", "qp_factor_K0", "qp_kf_apply", "qp_k0_solve", "qp_pcg_reduced_solve",
+                 "qp_ipm_solve", "qp_get_stats", "qp_time_pcg_iteration"):
+        getattr(lib, name).restype = I
+    _lib = lib
+    return lib
+
+
+class QPError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {qp_strerror(status)} ({status})")
+
+
+def _check(st, where, ok=(QP_OK,)):
+    if st not in ok:
+        raise QPError(st, where)
+    return st
+
+
+def _ptr(a, kind_holder):
+    """Raw pointer of a float64 array (numpy host or torch CUDA), recording its kind."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError("host arrays must be C-contiguous float64")
+        kind = QP_PTR_HOST
+        p = a.ctypes.data
+    else:  # torch tensor
+        if str(a.dtype) != "torch.float64" or not a.is_contiguous():
+            raise TypeError("device tensors must be contiguous float64")
+        kind = QP_PTR_DEVICE if a.is_cuda else QP_PTR_HOST
+        p = a.data_ptr()
+    if kind_holder and kind_holder[0] is not None and kind_holder[0] != kind:
+        raise TypeError("mixing host and device arrays in one call")
+    if kind_holder is not None:
+        kind_holder[0] = kind
+    return p
+
+
+def qp_opts_default() -> qp_opts:
+    o = qp_opts()
+    load().qp_opts_default(ct.byref(o))
+    return o
+
+
+def qp_strerror(status: int) -> str:
+    return load().qp_strerror(int(status)).decode()
+
+
+def qp_create(H, c, A, b, C, d, opts: qp_opts | None = None):
+    """Create a handle (returns an opaque c_void_p).  A/b may be None (m1 = 0)."""
+    kh = [None]
+    n = int(H.shape[0])
+    m1 = 0 if A is None else int(A.shape[0])
+    m2 = int(d.shape[0])
+    h = ct.c_void_p()
+    st = load().qp_create(ct.byref(h), n, m1, m2, _ptr(H, kh), _ptr(c, kh), _ptr(A, kh), _ptr(b, kh),
+                          _ptr(C, kh), _ptr(d, kh), ct.byref(opts) if opts is not None else None, kh[0])
+    _check(st, "qp_create")
+    return h
+
+
+def qp_factor_K0(h):
+    return _check(load().qp_factor_K0(h), "qp_factor_K0")
+
+
+def qp_kf_apply(h, D, p, q):
+    kh = [None]
+    args = (_ptr(D, kh), _ptr(p, kh), _ptr(q, kh))
+    return _check(load().qp_kf_apply(h, *args, kh[0]), "qp_kf_apply")
+
+
+def qp_k0_solve(h, u, w, a, b=None):
+    kh = [None]
+    args = (_ptr(u, kh), _ptr(w, kh), _ptr(a, kh), _ptr(b, kh))
+    return _check(load().qp_k0_solve(h, *args, kh[0]), "qp_k0_solve")
+
+
+def qp_pcg_reduced_solve(h, D, rhs, dnu, precond=QP_PC_AUTO, tol=1e-8, maxit=1000, allow_maxit=False):
+    """Returns (status, iterations, relative residual)."""
+    kh = [None]
+    args = (_ptr(D, kh), _ptr(rhs, kh), _ptr(dnu, kh))
+    it = ct.c_int(0)
+    rel = ct.c_double(0)
+    st = load().qp_pcg_reduced_solve(h, *args, int(precond), float(tol), int(maxit), ct.byref(it),
+                                     ct.byref(rel), kh[0])
+    _check(st, "qp_pcg_reduced_solve", ok=(QP_OK, QP_EMAXIT) if allow_maxit else (QP_OK,))
+    return st, it.value, rel.value
+
+
+def qp_ipm_solve(h, x=None, lam=None, nu=None, s=None, allow=(QP_OK,)):
+    """Returns (status, objective, ipm_iters, pcg_iters_total)."""
+    kh = [None]
+    args = (_ptr(x, kh), _ptr(lam, kh), _ptr(nu, kh), _ptr(s, kh))
+    kind = kh[0] if kh[0] is not None else QP_PTR_HOST
+    obj = ct.c_double(0)
+    it = ct.c_int(0)
+    pit = ct.c_longlong(0)
+    st = load().qp_ipm_solve(h, *args, ct.byref(obj), ct.byref(it), ct.byref(pit), kind)
+    _check(st, "qp_ipm_solve", ok=allow)
+    return st, obj.value, it.value, pit.value
+
+
+def qp_get_stats(h) -> dict:
+    s = qp_stats()
+    _check(load().qp_get_stats(h, ct.byref(s)), "qp_get_stats")
+    return s.as_dict()
+
+
+def qp_device_bytes(h) -> int:
+    return int(load().qp_device_bytes(h))
+
+
+def qp_pcg_bytes_per_iter(h, precond=QP_PC_AUTO) -> float:
+    return float(load().qp_pcg_bytes_per_iter(h, int(precond)))
+
+
+def qp_time_pcg_iteration(h, D, precond=QP_PC_AUTO, warmup=8, iters=64) -> float:
+    kh = [None]
+    pD = _ptr(D, kh)
+    ms = ct.c_double(0)
+    _check(load().qp_time_pcg_iteration(h, pD, int(precond), int(warmup), int(iters), ct.byref(ms), kh[0]),
+           "qp_time_pcg_iteration")
+    return ms.value
+
+
+def qp_kernel_launches() -> int:
+    return int(load().qp_kernel_launches())
+
+
+def qp_destroy(h):
+    if h:
+        load().qp_destroy(h)
+
+
+class QP:
+    """Owning wrapper of a handle: QP(qpgen.QP or arrays, opts)."""
+
+    def __init__(self, H, c, A, b, C, d, opts: qp_opts | None = None):
+        self.h = qp_create(H, c, A, b, C, d, opts)
+        self.n, self.m1, self.m2 = int(H.shape[0]), (0 if A is None else int(A.shape[0])), int(d.shape[0])
+
+    @classmethod
+    def from_qpgen(cls, q, opts=None):
+        A = q.A if q.m1 else None
+        b = q.b if q.m1 else None
+        return cls(np.ascontiguousarray(q.H), q.c, A, b, np.ascontiguousarray(q.C_dense()), q.d, opts)
+
+    def factor(self):
+        qp_factor_K0(self.h)
+        return self
+
+    def close(self):
+        if self.h:
+            qp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,425 @@
+// dense.cuh -- dense factorization kernels: tiled GEMM, blocked Cholesky with
+// in-place triangular inverse, transposes and conversions.
+//
+// These implement the setup phase of Sec. 4.1 (the factorization of the fixed
+// equality-only KKT matrix) and the per-iteration Cholesky of P_H (Sec. 5.2,
+// PH-KF: "perform a Cholesky factorization P_H = L L^T at every IPM iteration").
+// Every triangular factor is also inverted (W = L^{-1}) so that the triangular
+// solves inside PCG become parallel triangular matrix-vector products.
+#pragma once
+
+#include "common.cuh"
+
+namespace pcgipm {
+
+enum Tri { TRI_NONE = 0, TRI_LOWER = 1, TRI_UPPER = 2 };
+
+// ---------------------------------------------------------------- tiled GEMM
+// C[i,j] = alpha * sum_k opA(i,k) opB(k,j) + beta * C[i,j]
+//   opA(i,k) = A[i*sai + k*sak],  opB(k,j) = B[k*sbk + j*sbj]
+// a_tri / b_tri declare the zero pattern of the logical operand (the zeros are
+// present in memory; declaring them only skips work): lower = zero above the
+// diagonal, upper = zero below.  lower_out: only tiles/elements with j <= i.
+template <typename T>
+struct GemmArgs {
+    int M, N, K;
+    const T* A; long long sai, sak;
+    const T* B; long long sbk, sbj;
+    T* C; long long ldc;
+    T alpha, beta;
+    int a_tri, b_tri, lower_out;
+};
+
+template <typename T, int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__(256) gemm_kernel(const GemmArgs<T> g) {
+    PCG_COUNT_KERNEL();
+    static_assert((BM / TM) * (BN / TN) == 256, "256 threads");
+    __shared__ T As[2][BK][BM + 4];
+    __shared__ T Bs[2][BK][BN + 4];
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    if (g.lower_out && n0 > m0 + BM - 1) return;
+    int kLo = 0, kHi = g.K;
+    if (g.a_tri == TRI_LOWER) kHi = min(kHi, m0 + BM);
+    if (g.a_tri == TRI_UPPER) kLo = max(kLo, m0);
+    if (g.b_tri == TRI_LOWER) kLo = max(kLo, n0);
+    if (g.b_tri == TRI_UPPER) kHi = min(kHi, n0 + BN);
+    const int tid = threadIdx.x;
+    const int tx = tid % (BN / TN), ty = tid / (BN / TN);
+    T acc[TM][TN];
+#pragma unroll
+    for (int r = 0; r < TM; ++r)
+#pragma unroll
+        for (int c = 0; c < TN; ++c) acc[r][c] = T(0);
+
+    const bool a_m_contig = (g.sai == 1);
+    const bool b_n_contig = (g.sbj == 1);
+    constexpr int A_PER = BM * BK / 256, B_PER = BK * BN / 256;
+    T ra[A_PER], rb[B_PER];
+
+    auto load_regs = [&](int k0) {
+#pragma unroll
+        for (int t = 0; t < A_PER; ++t) {
+            const int e = tid + 256 * t;
+            int mm, kk;
+            if (a_m_contig) { mm = e % BM; kk = e / BM; } else { kk = e % BK; mm = e / BK; }
+            const int gi = m0 + mm, gk = k0 + kk;
+            ra[t] = (gi < g.M && gk < kHi && gk >= kLo) ? g.A[gi * g.sai + gk * g.sak] : T(0);
+        }
+#pragma unroll
+        for (int t = 0; t < B_PER; ++t) {
+            const int e = tid + 256 * t;
+            int kk, nn;
+            if (b_n_contig) { nn = e % BN; kk = e / BN; } else { kk = e % BK; nn = e / BK; }
+            const int gj = n0 + nn, gk = k0 + kk;
+            rb[t] = (gj < g.N && gk < kHi && gk >= kLo) ? g.B[gk * g.sbk + gj * g.sbj] : T(0);
+        }
+    };
+    auto store_smem = [&](int buf) {
+#pragma unroll
+        for (int t = 0; t < A_PER; ++t) {
+            const int e = tid + 256 * t;
+            int mm, kk;
+            if (a_m_contig) { mm = e % BM; kk = e / BM; } else { kk = e % BK; mm = e / BK; }
+            As[buf][kk][mm] = ra[t];
+        }
+#pragma unroll
+        for (int t = 0; t < B_PER; ++t) {
+            const int e = tid + 256 * t;
+            int kk, nn;
+            if (b_n_contig) { nn = e % BN; kk = e / BN; } else { kk = e % BK; nn = e / BK; }
+            Bs[buf][kk][nn] = rb[t];
+        }
+    };
+
+    int k0 = (kLo / BK) * BK;
+    if (k0 < kHi) {
+        load_regs(k0);
+        store_smem(0);
+        __syncthreads();
+        int buf = 0;
+        for (; k0 < kHi; k0 += BK) {
+            const bool more = (k0 + BK < kHi);
+            if (more) load_regs(k0 + BK);
+#pragma unroll
+            for (int kk = 0; kk < BK; ++kk) {
+                T a[TM], b[TN];
+#pragma unroll
+                for (int r = 0; r < TM; ++r) a[r] = As[buf][kk][ty + r * (BM / TM)];
+#pragma unroll
+                for (int c = 0; c < TN; ++c) b[c] = Bs[buf][kk][tx + c * (BN / TN)];
+#pragma unroll
+                for (int r = 0; r < TM; ++r)
+#pragma unroll
+                    for (int c = 0; c < TN; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+            }
+            if (more) {
+                store_smem(buf ^ 1);
+                __syncthreads();
+                buf ^= 1;
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < TM; ++r) {
+        const int i = m0 + ty + r * (BM / TM);
+        if (i >= g.M) continue;
+#pragma unroll
+        for (int c = 0; c < TN; ++c) {
+            const int j = n0 + tx + c * (BN / TN);
+            if (j >= g.N) continue;
+            if (g.lower_out && j > i) continue;
+            T* p = g.C + i * g.ldc + j;
+            T v = g.alpha * acc[r][c];
+            if (g.beta != T(0)) v = fma(g.beta, *p, v);
+            *p = v;
+        }
+    }
+}
+
+template <typename T>
+inline void gemm(const GemmArgs<T>& g, cudaStream_t s) {
+    if (g.M <= 0 || g.N <= 0) return;
+    if constexpr (sizeof(T) == 4) {
+        constexpr int BM = 128, BN = 128;
+        dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM);
+        gemm_kernel<T, BM, BN, 8, 8, 8><<<grid, 256, 0, s>>>(g);
+    } else {
+        constexpr int BM = 64, BN = 64;
+        dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM);
+        gemm_kernel<T, BM, BN, 16, 4, 4><<<grid, 256, 0, s>>>(g);
+    }
+}
+
+// ------------------------------------------------- blocked Cholesky + inverse
+constexpr int kNB = 64;   // block size of the blocked factorization
+
+// Factor the kb x kb diagonal block A[k0.., k0..] (lower) in compute type CT,
+// write L_kk back (upper part of the block zeroed) and W_kk = L_kk^{-1} into W.
+// floor_mode = 0: a pivot d <= piv_floor * diag0[k0+j] (diag0: the matrix's
+//   original diagonal; a non-positive or numerically zero pivot) records
+//   info = k0 + j + 1 (first failure wins) and continues with d = 1 so that the
+//   kernel stays finite.
+// floor_mode = 1: a pivot d < piv_floor is replaced by piv_floor (a diagonal
+//   shift of a preconditioner; counted in info as a positive number of shifts).
+template <typename T, typename CT>
+__global__ void __launch_bounds__(256) potrf_diag_kernel(T* A, long long lda, T* W, long long ldw,
+                                                         int k0, int kb, int floor_mode,
+                                                         double piv_floor, int* info,
+                                                         const double* __restrict__ diag0) {
+    PCG_COUNT_KERNEL();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    auto a = reinterpret_cast<CT(*)[kNB + 1]>(smem_raw);
+    auto w = reinterpret_cast<CT(*)[kNB + 1]>(smem_raw + sizeof(CT) * kNB * (kNB + 1));
+    __shared__ CT piv;
+    const int tid = threadIdx.x;
+    for (int e = tid; e < kb * kb; e += 256) {
+        const int i = e / kb, j = e % kb;
+        a[i][j] = (j <= i) ? CT(A[(k0 + i) * lda + k0 + j]) : CT(0);
+    }
+    __syncthreads();
+    for (int j = 0; j < kb; ++j) {
+        if (tid == 0) {
+            CT d = a[j][j];
+            if (floor_mode == 0) {
+                if (!(d > CT(piv_floor * diag0[k0 + j]))) {
+                    atomicCAS(info, 0, k0 + j + 1);
+                    d = CT(1);
+                }
+            } else if (!(d >= CT(piv_floor))) {
+                atomicAdd(info, 1);
+                d = CT(piv_floor);
+            }
+            piv = sqrt(d);
+            a[j][j] = piv;
+        }
+        __syncthreads();
+        const CT inv = CT(1) / piv;
+        for (int i = j + 1 + tid; i < kb; i += 256) a[i][j] *= inv;
+        __syncthreads();
+        const int rem = kb - j - 1;
+        for (int e = tid; e < rem * rem; e += 256) {
+            const int i = j + 1 + e / rem, l = j + 1 + e % rem;
+            if (l <= i) a[i][l] -= a[i][j] * a[l][j];
+        }
+        __syncthreads();
+    }
+    // W = L^{-1}: thread t solves L w_t = e_t (column t) by forward substitution.
+    if (tid < kb) {
+        const int t = tid;
+        for (int i = 0; i < t; ++i) w[i][t] = CT(0);
+        w[t][t] = CT(1) / a[t][t];
+        for (int i = t + 1; i < kb; ++i) {
+            CT s = CT(0);
+            for (int k = t; k < i; ++k) s += a[i][k] * w[k][t];
+            w[i][t] = -s / a[i][i];
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < kb * kb; e += 256) {
+        const int i = e / kb, j = e % kb;
+        A[(k0 + i) * lda + k0 + j] = (j <= i) ? T(a[i][j]) : T(0);
+        W[(k0 + i) * ldw + k0 + j] = (j <= i) ? T(w[i][j]) : T(0);
+    }
+}
+
+// Panel of the right-looking Cholesky: A[r, k0:k0+kb] <- A[r, k0:k0+kb] W_kk^T
+// for rows r in [k0+kb, n), in place (one CTA per 64-row slab).
+template <typename T>
+__global__ void __launch_bounds__(256) trsm_panel_kernel(T* A, long long lda, const T* W, long long ldw,
+                                                         int k0, int kb, int n) {
+    PCG_COUNT_KERNEL();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    auto wk = reinterpret_cast<T(*)[kNB + 1]>(smem_raw);
+    auto ap = reinterpret_cast<T(*)[kNB + 1]>(smem_raw + sizeof(T) * kNB * (kNB + 1));
+    const int r0 = k0 + kb + blockIdx.x * kNB;
+    const int tid = threadIdx.x;
+    for (int e = tid; e < kb * kb; e += 256) {
+        const int i = e / kb, j = e % kb;
+        wk[i][j] = W[(k0 + i) * ldw + k0 + j];
+    }
+    for (int e = tid; e < kNB * kb; e += 256) {
+        const int i = e / kb, j = e % kb;
+        ap[i][j] = (r0 + i < n) ? A[(r0 + i) * lda + k0 + j] : T(0);
+    }
+    __syncthreads();
+    // out[i][j] = sum_{l <= j} ap[i][l] * wk[j][l]   (W lower => W^T upper)
+    for (int e = tid; e < kNB * kb; e += 256) {
+        const int i = e / kb, j = e % kb;
+        if (r0 + i >= n) continue;
+        T s = T(0);
+        for (int l = 0; l <= j; ++l) s = fma(ap[i][l], wk[j][l], s);
+        A[(r0 + i) * lda + k0 + j] = s;
+    }
+}
+
+// Right-looking triangular inverse, scaling step: W[k0:k0+kb, 0:k0] <- W_kk W[k0:k0+kb, 0:k0]
+// (in place, one CTA per 64-column slab; W_kk lower).
+template <typename T>
+__global__ void __launch_bounds__(256) trmm_rowblock_kernel(T* W, long long ldw, int k0, int kb) {
+    PCG_COUNT_KERNEL();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    auto wk = reinterpret_cast<T(*)[kNB + 1]>(smem_raw);
+    auto rs = reinterpret_cast<T(*)[kNB + 1]>(smem_raw + sizeof(T) * kNB * (kNB + 1));
+    const int c0 = blockIdx.x * kNB;
+    const int cw = min(kNB, k0 - c0);
+    const int tid = threadIdx.x;
+    for (int e = tid; e < kb * kb; e += 256) {
+        const int i = e / kb, j = e % kb;
+        wk[i][j] = W[(k0 + i) * ldw + k0 + j];
+    }
+    for (int e = tid; e < kb * cw; e += 256) {
+        const int i = e / cw, j = e % cw;
+        rs[i][j] = W[(k0 + i) * ldw + c0 + j];
+    }
+    __syncthreads();
+    for (int e = tid; e < kb * cw; e += 256) {
+        const int i = e / cw, j = e % cw;
+        T s = T(0);
+        for (int l = 0; l <= i; ++l) s = fma(wk[i][l], rs[l][j], s);
+        W[(k0 + i) * ldw + c0 + j] = s;
+    }
+}
+
+// In-place blocked Cholesky of the lower triangle of A (n x n, leading dim lda)
+// and its inverse W = L^{-1} (lower, zeros above the diagonal; W must be
+// zero-initialised by the caller).  CT is the compute type of the diagonal
+// blocks (double: FP64 pivots).  Right-looking: per block column k
+//   1. factor the diagonal block and invert it,
+//   2. panel  L21 = A21 W_kk^T,
+//   3. trailing update A22 -= L21 L21^T (lower tiles),
+//   4. inverse: W[k, 0:k] <- W_kk R[k, 0:k];  R[k+1:, 0:k+1] -= L21 W[k, 0:k+1].
+// Dynamic shared memory of the three block kernels: two (kNB x kNB+1) tiles.
+template <typename X>
+constexpr size_t two_tiles_bytes() { return 2 * sizeof(X) * kNB * (kNB + 1); }
+
+template <typename T, typename CT>
+inline void chol_inv_prepare() {
+    cudaFuncSetAttribute(potrf_diag_kernel<T, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)two_tiles_bytes<CT>());
+    cudaFuncSetAttribute(trsm_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)two_tiles_bytes<T>());
+    cudaFuncSetAttribute(trmm_rowblock_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)two_tiles_bytes<T>());
+}
+
+template <typename T>
+__global__ void save_diag_kernel(const T* __restrict__ A, long long lda, int n, double* __restrict__ out) {
+    PCG_COUNT_KERNEL();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        out[i] = (double)A[i * lda + i];
+}
+
+// diag0: scratch of n doubles (used when floor_mode == 0).
+template <typename T, typename CT>
+void chol_inv(T* A, long long lda, T* W, long long ldw, int n, int floor_mode, double piv_floor,
+              int* d_info, cudaStream_t s, double* diag0 = nullptr) {
+    if (floor_mode == 0) save_diag_kernel<T><<<(n + 255) / 256, 256, 0, s>>>(A, lda, n, diag0);
+    for (int k0 = 0; k0 < n; k0 += kNB) {
+        const int kb = min(kNB, n - k0);
+        potrf_diag_kernel<T, CT><<<1, 256, two_tiles_bytes<CT>(), s>>>(A, lda, W, ldw, k0, kb,
+                                                                      floor_mode, piv_floor, d_info, diag0);
+        const int rest = n - k0 - kb;
+        if (k0 > 0) {
+            trmm_rowblock_kernel<T><<<(k0 + kNB - 1) / kNB, 256, two_tiles_bytes<T>(), s>>>(W, ldw, k0, kb);
+        }
+        if (rest > 0) {
+            trsm_panel_kernel<T><<<(rest + kNB - 1) / kNB, 256, two_tiles_bytes<T>(), s>>>(A, lda, W, ldw,
+                                                                                          k0, kb, n);
+            GemmArgs<T> g{};
+            // trailing update A22 -= L21 L21^T
+            g.M = rest; g.N = rest; g.K = kb;
+            g.A = A + (k0 + kb) * lda + k0; g.sai = lda; g.sak = 1;
+            g.B = A + (k0 + kb) * lda + k0; g.sbk = 1; g.sbj = lda;
+            g.C = A + (k0 + kb) * lda + k0 + kb; g.ldc = lda;
+            g.alpha = T(-1); g.beta = T(1); g.lower_out = 1;
+            gemm<T>(g, s);
+            // inverse update R[k+1:, 0:k0+kb] -= L21 W[k0:k0+kb, 0:k0+kb]
+            GemmArgs<T> h{};
+            h.M = rest; h.N = k0 + kb; h.K = kb;
+            h.A = A + (k0 + kb) * lda + k0; h.sai = lda; h.sak = 1;
+            h.B = W + k0 * ldw; h.sbk = ldw; h.sbj = 1;
+            h.C = W + (k0 + kb) * ldw; h.ldc = ldw;
+            h.alpha = T(-1); h.beta = T(1);
+            gemm<T>(h, s);
+        }
+    }
+}
+
+// ------------------------------------------------------------- small helpers
+template <typename T>
+__global__ void transpose_kernel(const T* __restrict__ in, long long ldi, T* __restrict__ out,
+                                 long long ldo, int rows, int cols) {
+    PCG_COUNT_KERNEL();
+    __shared__ T tile[32][33];
+    const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += 8) {
+        const int i = by + r, j = bx + threadIdx.x;
+        if (i < rows && j < cols) tile[r][threadIdx.x] = in[i * ldi + j];
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += 8) {
+        const int j = bx + r, i = by + threadIdx.x;
+        if (i < rows && j < cols) out[j * ldo + i] = tile[threadIdx.x][r];
+    }
+}
+
+template <typename T>
+inline void transpose(const T* in, long long ldi, T* out, long long ldo, int rows, int cols,
+                      cudaStream_t s) {
+    if (rows <= 0 || cols <= 0) return;
+    dim3 grid((cols + 31) / 32, (rows + 31) / 32), block(32, 8);
+    transpose_kernel<T><<<grid, block, 0, s>>>(in, ldi, out, ldo, rows, cols);
+}
+
+// out[i*ldo + j] = (TO) in[i*ldi + j] * (colscale ? colscale[j] : 1)
+template <typename TI, typename TO>
+__global__ void convert2d_kernel(const TI* __restrict__ in, long long ldi, TO* __restrict__ out,
+                                 long long ldo, int rows, int cols, const double* __restrict__ colscale) {
+    PCG_COUNT_KERNEL();
+    const long long total = (long long)rows * cols;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / cols), j = (int)(e % cols);
+        double v = (double)in[i * ldi + j];
+        if (colscale) v *= colscale[j];
+        out[i * ldo + j] = (TO)v;
+    }
+}
+
+template <typename TI, typename TO>
+inline void convert2d(const TI* in, long long ldi, TO* out, long long ldo, int rows, int cols,
+                      cudaStream_t s, const double* colscale = nullptr) {
+    if (rows <= 0 || cols <= 0) return;
+    long long total = (long long)rows * cols;
+    long long want = (total + 255) / 256;
+    int blocks = (int)(want < 152LL * 16 ? want : 152LL * 16);
+    convert2d_kernel<TI, TO><<<blocks, 256, 0, s>>>(in, ldi, out, ldo, rows, cols, colscale);
+}
+
+// Jacobi-scaled preconditioner matrix P~ = Sg (D + T) Sg + shift I, Sg = diag(D + T)^{-1/2}
+// (lower triangle), and sg = diag(Sg).
+template <typename T>
+__global__ void build_scaled_ph_kernel(const T* __restrict__ Tm, long long ldt, const T* __restrict__ D,
+                                       T* __restrict__ P, long long ldp, T* __restrict__ sg, int m,
+                                       double shift) {
+    PCG_COUNT_KERNEL();
+    const long long total = (long long)m * m;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(e / m), j = (int)(e % m);
+        if (j > i) continue;
+        const double di = (double)Tm[i * ldt + i] + (double)D[i];
+        const double dj = (double)Tm[j * ldt + j] + (double)D[j];
+        const double si = 1.0 / sqrt(di), sj = 1.0 / sqrt(dj);
+        double v = (double)Tm[i * ldt + j];
+        if (i == j) {
+            v = 1.0 + shift;
+            sg[i] = (T)si;
+        } else {
+            v *= si * sj;
+        }
+        P[i * ldp + j] = (T)v;
+    }
+}
+
+}  // namespace pcgipm

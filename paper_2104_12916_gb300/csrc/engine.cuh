@@ -1,0 +1,1086 @@
+// engine.cuh -- one QP on one GPU: setup factorization, the implicit K_F
+// product, graph-captured PCG, reduced Newton solves with FP64 refinement and
+// the primal-dual IPM loop.
+//
+// Precisions.  The operator of the hot path (C, C' and the stored K0 factor,
+// with the PCG vectors) runs in TO; the factored preconditioner P_H in TP;
+// everything the IPM decides with (residuals, refinement residuals, step
+// lengths, centrality) is FP64.
+//   QP_PREC_FP64: TO = TP = double.
+//   QP_PREC_FP32: TP = float; TO starts as float and a QP switches to TO =
+//   double (a second, FP64 factor of K0) once FP64 refinement of a Newton
+//   direction contracts too slowly -- the FP32 operator's error is amplified by
+//   the conditioning of K_F on the active set late in the IPM.
+#pragma once
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <type_traits>
+#include <vector>
+
+#include "../../include/pcgipm.h"
+#include "common.cuh"
+#include "dense.cuh"
+#include "gemv.cuh"
+#include "vec.cuh"
+
+namespace pcgipm {
+
+struct CudaError { cudaError_t e; };
+struct NoMem {};
+struct QpError { int code; };
+
+#define PCG_CK(x)                                             \
+    do {                                                      \
+        cudaError_t _e = (x);                                 \
+        if (_e != cudaSuccess) throw ::pcgipm::CudaError{_e}; \
+    } while (0)
+
+// Owns every device allocation of one handle (zero-initialised).
+class DevArena {
+public:
+    ~DevArena() { release(); }
+    template <typename T>
+    T* alloc(size_t count) {
+        void* p = nullptr;
+        const size_t bytes = count * sizeof(T) + 256;
+        if (cudaMalloc(&p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            throw NoMem{};
+        }
+        PCG_CK(cudaMemset(p, 0, bytes));
+        ptrs_.push_back(p);
+        bytes_ += bytes;
+        return static_cast<T*>(p);
+    }
+    void release() {
+        for (void* p : ptrs_) cudaFree(p);
+        ptrs_.clear();
+    }
+    size_t bytes() const { return bytes_; }
+
+private:
+    std::vector<void*> ptrs_;
+    size_t bytes_ = 0;
+};
+
+template <typename T>
+struct Mat {
+    T* p = nullptr;
+    int rows = 0, cols = 0;
+    long long ld = 0;
+    void alloc(DevArena& a, int r, int c) {
+        rows = r;
+        cols = c;
+        ld = pad_ld(c > 0 ? c : 1);
+        p = a.alloc<T>((size_t)(r > 0 ? r : 1) * ld);
+    }
+};
+
+// y_i = a acc + b z_i + c w_i + e dv_i dx_i  (optional terms skipped when null)
+template <typename T>
+struct EpiLin {
+    T* y;
+    T a;
+    const T* z; T b;
+    const T* w; T c;
+    const T* dv; const T* dx; T e;
+    __device__ __forceinline__ double operator()(int i, T acc) const {
+        T v = a * acc;
+        if (z) v += b * z[i];
+        if (w) v += c * w[i];
+        if (dv) v += e * dv[i] * dx[i];
+        y[i] = v;
+        return 0.0;
+    }
+};
+
+template <typename T>
+inline EpiLin<T> lin(T* y, T a = T(1), const T* z = nullptr, T b = T(0), const T* w = nullptr, T c = T(0),
+                     const T* dv = nullptr, const T* dx = nullptr, T e = T(0)) {
+    return EpiLin<T>{y, a, z, b, w, c, dv, dx, e};
+}
+
+inline int resolve_pc(int pc, int n, int m1) {
+    if (pc == QP_PC_AUTO) return (2 * m1 >= n) ? QP_PC_PL : QP_PC_PH_EXACT;
+    return pc;
+}
+
+inline int pc_kind(int pc) {
+    if (pc == QP_PC_PL) return PC_L_K;
+    if (pc == QP_PC_PH_EXACT || pc == QP_PC_PH_DIAG) return PC_H_K;
+    return PC_NONE_K;
+}
+
+// Operator of the hot path in precision TO: C, C', the inverted K0 factor, and
+// the PCG / K0-solve vectors.
+template <typename TO>
+struct Op {
+    Mat<TO> CW, CWT;   // C and C'
+    Mat<TO> WH, WHT;   // R^{-T} = L_H^{-1} (lower) and R^{-1} (upper), H = R'R
+    Mat<TO> Gt, GtT;   // L_S^{-1} A R^{-1} and its transpose, L_S L_S' = A H^{-1} A'
+    Mat<TO> WS, WST;   // L_S^{-1} (lower) and L_S^{-T} (upper)
+    TO *px = nullptr, *pr, *pz, *pp, *pq, *pu, *pz1, *pz2, *pt, *py, *prhs, *pD, *pDinv;
+    TO *ku, *kw, *ke, *kz1, *kz2, *kt, *ka, *kmb, *wa, *wg;
+    cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
+    int graph_k[3] = {0, 0, 0};
+    bool factored = false;
+};
+
+// Factored preconditioner P_H in precision TP.
+template <typename TP>
+struct Pc {
+    Mat<TP> Tm, Pm, WPl, WPu;   // T = C H^{-1} C' (or C diag(H)^{-1} C'), P~, L^{-1}, L^{-T}
+    TP *sg = nullptr, *rs, *pv, *Dp;
+    int t_kind = 0;
+    double shift = 0.0;
+};
+
+class Engine {
+public:
+    int n = 0, m1 = 0, m2 = 0;
+    qp_opts opt{};
+    cudaStream_t s = nullptr;
+    bool own_stream = false;
+    bool factored = false;
+    bool f64 = false;       // QP_PREC_FP64
+    bool use64 = false;     // operator currently in FP64
+    DevArena arena;
+    qp_stats stats{};
+    double* stage[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool verbose = false;
+    int ipm_k = 0;
+
+    // FP64 problem data (masters for residuals and refinement)
+    Mat<double> H, A, AT, C, CT;
+    double *c = nullptr, *b = nullptr, *d = nullptr;
+    double h_norm_inf = 0, b_inf = 0, c_inf = 0, d_inf = 0;
+
+    Op<float> o32;
+    Op<double> o64;
+    Pc<float> p32;
+    Pc<double> p64;
+
+    double *part_pq, *part_rr, *part_rz, *part_bb, *part_a, *part_b, *part_c, *part_d, *part_e, *part_f, *diag0;
+    PcgState* st = nullptr;
+    PcgState* hst = nullptr;   // pinned, 2 slots
+    double* d_scal = nullptr;
+    double* h_scal = nullptr;  // pinned
+    int* d_info = nullptr;
+    int* h_info = nullptr;     // pinned
+    cudaEvent_t ev0, ev1, evA, evB;
+    int cap_rows = 0;
+    int last_pcg_done = 0;
+    double last_pcg_rel = 0.0;
+
+    // FP64 IPM vectors
+    double *x, *lam, *nu, *sl, *hx, *rg, *re, *ri, *rc, *ra, *D64;
+    double *dx, *dl, *dn, *ds, *dxa, *dla, *dna, *dsa;
+    double *fg, *fe, *fa, *rho_g, *rho_e, *rho_a, *tx, *tl, *tn;
+
+    template <typename TO> Op<TO>& op() {
+        if constexpr (std::is_same<TO, float>::value) return o32; else return o64;
+    }
+    template <typename TP> Pc<TP>& pcd() {
+        if constexpr (std::is_same<TP, float>::value) return p32; else return p64;
+    }
+
+    Engine(int n_, int m1_, int m2_, const qp_opts& o) {
+        n = n_; m1 = m1_; m2 = m2_; opt = o;
+        f64 = (opt.precision == QP_PREC_FP64);
+        use64 = f64;
+        if (opt.stream) {
+            s = static_cast<cudaStream_t>(opt.stream);
+        } else {
+            PCG_CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+            own_stream = true;
+        }
+        PCG_CK(cudaEventCreate(&ev0));
+        PCG_CK(cudaEventCreate(&ev1));
+        PCG_CK(cudaEventCreate(&evA));
+        PCG_CK(cudaEventCreate(&evB));
+        cap_rows = std::max(std::max(n, m2), std::max(m1, 512)) + 64;   // >= every partials grid
+        const char* v = std::getenv("PCGIPM_VERBOSE");
+        verbose = v && v[0] == '1';
+    }
+
+    template <typename TO>
+    void destroy_graphs(Op<TO>& o) {
+        for (auto& g : o.graph)
+            if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+    }
+
+    ~Engine() {
+        destroy_graphs(o32);
+        destroy_graphs(o64);
+        if (hst) cudaFreeHost(hst);
+        if (h_scal) cudaFreeHost(h_scal);
+        if (h_info) cudaFreeHost(h_info);
+        cudaEventDestroy(ev0);
+        cudaEventDestroy(ev1);
+        cudaEventDestroy(evA);
+        cudaEventDestroy(evB);
+        arena.release();
+        if (own_stream) cudaStreamDestroy(s);
+    }
+
+    template <typename X>
+    X* vec(int len) { return arena.alloc<X>((size_t)pad_ld(len > 0 ? len : 1)); }
+
+    void sync_check() {
+        PCG_CK(cudaStreamSynchronize(s));
+        PCG_CK(cudaGetLastError());
+    }
+
+    // ------------------------------------------------------------------ create
+    void load(const double* Hh, const double* ch, const double* Ah, const double* bh, const double* Ch,
+              const double* dh, int ptr_kind) {
+        const cudaMemcpyKind kind = (ptr_kind == QP_PTR_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        H.alloc(arena, n, n);
+        A.alloc(arena, m1, n);
+        AT.alloc(arena, n, m1);
+        C.alloc(arena, m2, n);
+        CT.alloc(arena, n, m2);
+        c = vec<double>(n); b = vec<double>(m1); d = vec<double>(m2);
+        PCG_CK(cudaMemcpy2DAsync(H.p, H.ld * 8, Hh, (size_t)n * 8, (size_t)n * 8, n, kind, s));
+        if (m1) PCG_CK(cudaMemcpy2DAsync(A.p, A.ld * 8, Ah, (size_t)n * 8, (size_t)n * 8, m1, kind, s));
+        PCG_CK(cudaMemcpy2DAsync(C.p, C.ld * 8, Ch, (size_t)n * 8, (size_t)n * 8, m2, kind, s));
+        PCG_CK(cudaMemcpyAsync(c, ch, (size_t)n * 8, kind, s));
+        if (m1) PCG_CK(cudaMemcpyAsync(b, bh, (size_t)m1 * 8, kind, s));
+        PCG_CK(cudaMemcpyAsync(d, dh, (size_t)m2 * 8, kind, s));
+        transpose<double>(A.p, A.ld, AT.p, AT.ld, m1, n, s);
+        transpose<double>(C.p, C.ld, CT.p, CT.ld, m2, n, s);
+
+        part_pq = vec<double>(cap_rows); part_rr = vec<double>(cap_rows); part_rz = vec<double>(cap_rows);
+        part_bb = vec<double>(cap_rows); part_a = vec<double>(cap_rows); part_b = vec<double>(cap_rows);
+        part_c = vec<double>(cap_rows); part_d = vec<double>(cap_rows); part_e = vec<double>(cap_rows);
+        part_f = vec<double>(cap_rows); diag0 = vec<double>(cap_rows);
+        st = arena.alloc<PcgState>(1);
+        d_scal = vec<double>(16);
+        d_info = arena.alloc<int>(8);
+        PCG_CK(cudaMallocHost(&hst, 2 * sizeof(PcgState)));
+        PCG_CK(cudaMallocHost(&h_scal, 16 * sizeof(double)));
+        PCG_CK(cudaMallocHost(&h_info, 8 * sizeof(int)));
+        for (auto& p : stage) p = vec<double>(cap_rows);
+
+        // validation: finiteness and symmetry of H
+        PCG_CK(cudaMemsetAsync(d_info, 0, 8 * sizeof(int), s));
+        nonfinite_kernel<<<304, 256, 0, s>>>((long long)n * H.ld, H.p, d_info);
+        if (m1) nonfinite_kernel<<<304, 256, 0, s>>>((long long)m1 * A.ld, A.p, d_info);
+        nonfinite_kernel<<<304, 256, 0, s>>>((long long)m2 * C.ld, C.p, d_info);
+        nonfinite_kernel<<<64, 256, 0, s>>>(n, c, d_info);
+        if (m1) nonfinite_kernel<<<64, 256, 0, s>>>(m1, b, d_info);
+        nonfinite_kernel<<<64, 256, 0, s>>>(m2, d, d_info);
+        asym_kernel<<<304, 256, 0, s>>>(n, H.p, H.ld, reinterpret_cast<unsigned int*>(d_info + 1));
+        // norms used by the stopping rule
+        absrowsum_max_kernel<<<152, 256, 0, s>>>(n, H.p, H.ld, part_a);
+        norms_kernel<<<vec_grid(n), kVecThreads, 0, s>>>(n, c, part_b, part_c);
+        norms_kernel<<<vec_grid(std::max(m1, 1)), kVecThreads, 0, s>>>(m1, b, part_b, part_d);
+        norms_kernel<<<vec_grid(m2), kVecThreads, 0, s>>>(m2, d, part_b, part_e);
+        ReduceJob job{};
+        job.part[0] = part_a; job.cnt[0] = 152; job.op[0] = 1;
+        job.part[1] = part_c; job.cnt[1] = vec_grid(n); job.op[1] = 1;
+        job.part[2] = part_d; job.cnt[2] = vec_grid(std::max(m1, 1)); job.op[2] = 1;
+        job.part[3] = part_e; job.cnt[3] = vec_grid(m2); job.op[3] = 1;
+        job.njobs = 4;
+        reduce_jobs_kernel<<<1, kVecThreads, 0, s>>>(job, d_scal);
+        PCG_CK(cudaMemcpyAsync(h_scal, d_scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        PCG_CK(cudaMemcpyAsync(h_info, d_info, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        sync_check();
+        h_norm_inf = h_scal[0]; c_inf = h_scal[1]; b_inf = m1 ? h_scal[2] : 0.0; d_inf = h_scal[3];
+        float asym;
+        std::memcpy(&asym, &h_info[1], sizeof(float));
+        if (h_info[0] != 0 || !(asym <= 1e-12f)) throw QpError{QP_EINVAL};
+
+        // IPM vectors
+        x = vec<double>(n); lam = vec<double>(m1); nu = vec<double>(m2); sl = vec<double>(m2);
+        hx = vec<double>(n); rg = vec<double>(n); re = vec<double>(m1); ri = vec<double>(m2);
+        rc = vec<double>(m2); ra = vec<double>(m2); D64 = vec<double>(m2);
+        dx = vec<double>(n); dl = vec<double>(m1); dn = vec<double>(m2); ds = vec<double>(m2);
+        dxa = vec<double>(n); dla = vec<double>(m1); dna = vec<double>(m2); dsa = vec<double>(m2);
+        fg = vec<double>(n); fe = vec<double>(m1); fa = vec<double>(m2);
+        rho_g = vec<double>(n); rho_e = vec<double>(m1); rho_a = vec<double>(m2);
+        tx = vec<double>(n); tl = vec<double>(m1); tn = vec<double>(m2);
+        sync_check();
+    }
+
+    // ------------------------------------------------------------------ factor
+    // Setup phase (Sec. 4.1): K0 = [H A'; A 0] = L diag(I, -I) L' with
+    // L = [R' 0; G L_S], R'R = H, G = A R^{-1}, L_S L_S' = G G' = A H^{-1} A'.
+    // The diagonal blocks are factored with FP64 pivots; a pivot below
+    // 1e-13 (FP64) / 1e-6 (FP32) of the original diagonal entry means H is not
+    // positive definite (QP_ENOTCONVEX) or A H^{-1} A' is singular (QP_ESINGULAR).
+    template <typename TO>
+    void factor_op() {
+        Op<TO>& o = op<TO>();
+        if (o.factored) return;
+        constexpr bool is64 = std::is_same<TO, double>::value;
+        const double rel = is64 ? 1e-13 : 1e-6;
+        chol_inv_prepare<TO, double>();
+        if (!o.px) {
+            o.px = vec<TO>(m2); o.pr = vec<TO>(m2); o.pz = vec<TO>(m2); o.pp = vec<TO>(m2); o.pq = vec<TO>(m2);
+            o.pu = vec<TO>(n); o.pz1 = vec<TO>(n); o.pz2 = vec<TO>(m1); o.pt = vec<TO>(n); o.py = vec<TO>(n);
+            o.prhs = vec<TO>(m2); o.pD = vec<TO>(m2); o.pDinv = vec<TO>(m2);
+            o.ku = vec<TO>(n); o.kw = vec<TO>(m1); o.ke = vec<TO>(m1); o.kz1 = vec<TO>(n); o.kz2 = vec<TO>(m1);
+            o.kt = vec<TO>(n); o.ka = vec<TO>(n); o.kmb = vec<TO>(m1); o.wa = vec<TO>(m2); o.wg = vec<TO>(n);
+            if constexpr (is64) {
+                o.CW.p = C.p; o.CW.rows = m2; o.CW.cols = n; o.CW.ld = C.ld;
+                o.CWT.p = CT.p; o.CWT.rows = n; o.CWT.cols = m2; o.CWT.ld = CT.ld;
+            } else {
+                o.CW.alloc(arena, m2, n);
+                o.CWT.alloc(arena, n, m2);
+                convert2d<double, TO>(C.p, C.ld, o.CW.p, o.CW.ld, m2, n, s);
+                convert2d<double, TO>(CT.p, CT.ld, o.CWT.p, o.CWT.ld, n, m2, s);
+            }
+            o.WH.alloc(arena, n, n);
+            o.WHT.alloc(arena, n, n);
+            if (m1) {
+                o.WS.alloc(arena, m1, m1); o.WST.alloc(arena, m1, m1);
+                o.Gt.alloc(arena, m1, n); o.GtT.alloc(arena, n, m1);
+            }
+        }
+        // scratch of the factorization (freed at the end)
+        TO *Hw = nullptr, *Aw = nullptr, *G = nullptr, *S = nullptr;
+        const long long ldn = pad_ld(n), ldm = pad_ld(std::max(m1, 1));
+        auto galloc = [&](TO** p, size_t count) {
+            if (cudaMalloc(p, count * sizeof(TO) + 256) != cudaSuccess) { cudaGetLastError(); throw NoMem{}; }
+            PCG_CK(cudaMemsetAsync(*p, 0, count * sizeof(TO) + 256, s));
+        };
+        galloc(&Hw, (size_t)n * ldn);
+        PCG_CK(cudaMemsetAsync(o.WH.p, 0, (size_t)n * o.WH.ld * sizeof(TO), s));
+        convert2d<double, TO>(H.p, H.ld, Hw, ldn, n, n, s);
+        PCG_CK(cudaMemsetAsync(d_info, 0, 8 * sizeof(int), s));
+        chol_inv<TO, double>(Hw, ldn, o.WH.p, o.WH.ld, n, 0, rel, d_info, s, diag0);
+        transpose<TO>(o.WH.p, o.WH.ld, o.WHT.p, o.WHT.ld, n, n, s);
+        if (m1) {
+            galloc(&Aw, (size_t)m1 * ldn);
+            galloc(&G, (size_t)m1 * ldn);
+            galloc(&S, (size_t)m1 * ldm);
+            PCG_CK(cudaMemsetAsync(o.WS.p, 0, (size_t)m1 * o.WS.ld * sizeof(TO), s));
+            convert2d<double, TO>(A.p, A.ld, Aw, ldn, m1, n, s);
+            GemmArgs<TO> g{};
+            // G = A R^{-1} = A WH'   (opB(k,j) = WH[j,k], zero for k > j)
+            g.M = m1; g.N = n; g.K = n;
+            g.A = Aw; g.sai = ldn; g.sak = 1;
+            g.B = o.WH.p; g.sbk = 1; g.sbj = o.WH.ld; g.b_tri = TRI_UPPER;
+            g.C = G; g.ldc = ldn; g.alpha = TO(1); g.beta = TO(0);
+            gemm<TO>(g, s);
+            // S = G G'
+            GemmArgs<TO> h{};
+            h.M = m1; h.N = m1; h.K = n;
+            h.A = G; h.sai = ldn; h.sak = 1;
+            h.B = G; h.sbk = 1; h.sbj = ldn;
+            h.C = S; h.ldc = ldm; h.alpha = TO(1); h.beta = TO(0); h.lower_out = 1;
+            gemm<TO>(h, s);
+            chol_inv<TO, double>(S, ldm, o.WS.p, o.WS.ld, m1, 0, rel, d_info + 2, s, diag0);
+            // Gt = L_S^{-1} G
+            GemmArgs<TO> k{};
+            k.M = m1; k.N = n; k.K = m1;
+            k.A = o.WS.p; k.sai = o.WS.ld; k.sak = 1; k.a_tri = TRI_LOWER;
+            k.B = G; k.sbk = ldn; k.sbj = 1;
+            k.C = o.Gt.p; k.ldc = o.Gt.ld; k.alpha = TO(1); k.beta = TO(0);
+            gemm<TO>(k, s);
+            transpose<TO>(o.Gt.p, o.Gt.ld, o.GtT.p, o.GtT.ld, m1, n, s);
+            transpose<TO>(o.WS.p, o.WS.ld, o.WST.p, o.WST.ld, m1, m1, s);
+        }
+        PCG_CK(cudaMemcpyAsync(h_info, d_info, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        PCG_CK(cudaStreamSynchronize(s));
+        cudaFree(Hw);
+        if (Aw) cudaFree(Aw);
+        if (G) cudaFree(G);
+        if (S) cudaFree(S);
+        PCG_CK(cudaGetLastError());
+        if (h_info[0] != 0) throw QpError{QP_ENOTCONVEX};
+        if (h_info[2] != 0) throw QpError{QP_ESINGULAR};
+        o.factored = true;
+    }
+
+    void factor() {
+        if (factored) return;
+        PCG_CK(cudaEventRecord(evA, s));
+        if (f64) factor_op<double>(); else factor_op<float>();
+        const int pc = resolve_pc(opt.precond, n, m1);
+        if (pc_kind(pc) == PC_H_K) {
+            if (f64) ensure_T<double>(pc); else ensure_T<float>(pc);
+        }
+        PCG_CK(cudaEventRecord(evB, s));
+        PCG_CK(cudaEventSynchronize(evB));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, evA, evB);
+        stats.t_factor_ms = ms;
+        factored = true;
+    }
+
+    // T = C H^{-1} C' = (C R^{-1})(C R^{-1})' (exact) or C diag(H)^{-1} C' (diag),
+    // once per QP, from the operator factor of the same precision.
+    template <typename TP>
+    void ensure_T(int kind) {
+        Pc<TP>& P = pcd<TP>();
+        if (P.t_kind == kind) return;
+        factor_op<TP>();
+        Op<TP>& o = op<TP>();
+        if (!P.Tm.p) {
+            P.Tm.alloc(arena, m2, m2);
+            P.Pm.alloc(arena, m2, m2);
+            P.WPl.alloc(arena, m2, m2);
+            P.WPu.alloc(arena, m2, m2);
+            P.sg = vec<TP>(m2); P.rs = vec<TP>(m2); P.pv = vec<TP>(m2); P.Dp = vec<TP>(m2);
+            chol_inv_prepare<TP, TP>();
+        }
+        TP* Bp = nullptr;
+        const long long ldb = pad_ld(n);
+        if (cudaMalloc(&Bp, (size_t)m2 * ldb * sizeof(TP) + 256) != cudaSuccess) {
+            cudaGetLastError();
+            throw NoMem{};
+        }
+        if (kind == QP_PC_PH_EXACT) {
+            GemmArgs<TP> g{};
+            g.M = m2; g.N = n; g.K = n;
+            g.A = o.CW.p; g.sai = o.CW.ld; g.sak = 1;
+            g.B = o.WH.p; g.sbk = 1; g.sbj = o.WH.ld; g.b_tri = TRI_UPPER;
+            g.C = Bp; g.ldc = ldb; g.alpha = TP(1); g.beta = TP(0);
+            gemm<TP>(g, s);
+        } else {
+            double* hs = stage[3];
+            diag_rsqrt_kernel<<<vec_grid(n), kVecThreads, 0, s>>>(n, H.p, H.ld, hs);
+            convert2d<double, TP>(C.p, C.ld, Bp, ldb, m2, n, s, hs);
+        }
+        GemmArgs<TP> h{};
+        h.M = m2; h.N = m2; h.K = n;
+        h.A = Bp; h.sai = ldb; h.sak = 1;
+        h.B = Bp; h.sbk = 1; h.sbj = ldb;
+        h.C = P.Tm.p; h.ldc = P.Tm.ld; h.alpha = TP(1); h.beta = TP(0); h.lower_out = 1;
+        gemm<TP>(h, s);
+        PCG_CK(cudaStreamSynchronize(s));
+        cudaFree(Bp);
+        PCG_CK(cudaGetLastError());
+        P.t_kind = kind;
+    }
+
+    // P~ = Sg (D + T) Sg + shift I, Sg = diag(D + T)^{-1/2}; Cholesky and inverse
+    // (Sec. 5.2 PH-KF: P_H factored at every IPM iteration).  P~ is SPD in exact
+    // arithmetic, but late in the IPM its smallest eigenvalues (directions in
+    // null(T) with small D) fall below the working precision and the Cholesky
+    // meets pivots under the floor; it is then refactored with a diagonal shift
+    // (a preconditioner only needs to be SPD: the shift changes PCG iteration
+    // counts, never the solution).
+    template <typename TP>
+    void build_ph(const double* Dd) {
+        Pc<TP>& P = pcd<TP>();
+        constexpr bool is64 = std::is_same<TP, double>::value;
+        const double floor = is64 ? 1e-12 : 1e-5;
+        convert1d<double, TP>(m2, Dd, 1.0, P.Dp, s);
+        double shift = 0.0;
+        for (int attempt = 0; attempt < 6; ++attempt) {
+            build_scaled_ph_kernel<TP><<<304 * 4, 256, 0, s>>>(P.Tm.p, P.Tm.ld, P.Dp, P.Pm.p, P.Pm.ld, P.sg, m2, shift);
+            PCG_CK(cudaMemsetAsync(P.WPl.p, 0, (size_t)m2 * P.WPl.ld * sizeof(TP), s));
+            PCG_CK(cudaMemsetAsync(d_info + 4, 0, sizeof(int), s));
+            chol_inv<TP, TP>(P.Pm.p, P.Pm.ld, P.WPl.p, P.WPl.ld, m2, 1, floor, d_info + 4, s);
+            PCG_CK(cudaMemcpyAsync(h_info + 4, d_info + 4, sizeof(int), cudaMemcpyDeviceToHost, s));
+            sync_check();
+            if (h_info[4] == 0) break;
+            shift = (shift == 0.0) ? (is64 ? 1e-10 : 1e-4) : shift * 10.0;
+        }
+        transpose<TP>(P.WPl.p, P.WPl.ld, P.WPu.p, P.WPu.ld, m2, m2, s);
+        P.shift = shift;
+        if (verbose && shift > 0) std::fprintf(stderr, "  P_H shift %.1e\n", shift);
+    }
+
+    // ------------------------------------------------------- hot-path products
+    // [a; b] = K0^{-1} [u; w] with z1 = R^{-T} u, z2 = L_S^{-1} w - Gt z1,
+    // a = R^{-1}(z1 + Gt' z2), and mb = -b = L_S^{-T} z2 (forward solve, D^{-1},
+    // back solve of the LDL' factor).
+    template <typename TO>
+    void k0_solve_dev(const TO* u, const TO* w, TO* a, TO* mb, const int* skip = nullptr) {
+        Op<TO>& o = op<TO>();
+        launch_gemv<TO, TRI_LOWER>(o.WH.p, n, n, o.WH.ld, u, lin<TO>(o.kz1), nullptr, skip, s);
+        if (m1) {
+            if (w) {
+                launch_gemv<TO, TRI_LOWER>(o.WS.p, m1, m1, o.WS.ld, w, lin<TO>(o.ke), nullptr, skip, s);
+                launch_gemv<TO, TRI_NONE>(o.Gt.p, m1, n, o.Gt.ld, o.kz1, lin<TO>(o.kz2, TO(-1), o.ke, TO(1)), nullptr, skip, s);
+            } else {
+                launch_gemv<TO, TRI_NONE>(o.Gt.p, m1, n, o.Gt.ld, o.kz1, lin<TO>(o.kz2, TO(-1)), nullptr, skip, s);
+            }
+            launch_gemv<TO, TRI_NONE>(o.GtT.p, n, m1, o.GtT.ld, o.kz2, lin<TO>(o.kt, TO(1), o.kz1, TO(1)), nullptr, skip, s);
+            launch_gemv<TO, TRI_UPPER>(o.WHT.p, n, n, o.WHT.ld, o.kt, lin<TO>(a), nullptr, skip, s);
+            if (mb) launch_gemv<TO, TRI_UPPER>(o.WST.p, m1, m1, o.WST.ld, o.kz2, lin<TO>(mb), nullptr, skip, s);
+        } else {
+            launch_gemv<TO, TRI_UPPER>(o.WHT.p, n, n, o.WHT.ld, o.kz1, lin<TO>(a), nullptr, skip, s);
+        }
+    }
+
+    // q = K_F p = D p + C y, y = top block of K0^{-1} [C'p; 0]  (Sec. 5.2: a product
+    // with C', a solve with the factor of F, a product with C).  Returns the grid of
+    // the last GEMV (number of p'q partials in part_pq).
+    template <typename TO>
+    int kf_apply_dev(const TO* p, TO* q, const TO* Dw, const int* skip) {
+        Op<TO>& o = op<TO>();
+        launch_gemv<TO, TRI_NONE>(o.CWT.p, n, m2, o.CWT.ld, p, lin<TO>(o.pu), nullptr, skip, s);          // a6
+        launch_gemv<TO, TRI_LOWER>(o.WH.p, n, n, o.WH.ld, o.pu, lin<TO>(o.pz1), nullptr, skip, s);       // a7
+        const TO* top = o.pz1;
+        if (m1) {
+            launch_gemv<TO, TRI_NONE>(o.Gt.p, m1, n, o.Gt.ld, o.pz1, lin<TO>(o.pz2, TO(-1)), nullptr, skip, s);
+            launch_gemv<TO, TRI_NONE>(o.GtT.p, n, m1, o.GtT.ld, o.pz2, lin<TO>(o.pt, TO(1), o.pz1, TO(1)), nullptr, skip, s);
+            top = o.pt;
+        }
+        launch_gemv<TO, TRI_UPPER>(o.WHT.p, n, n, o.WHT.ld, top, lin<TO>(o.py), nullptr, skip, s);
+        return launch_gemv<TO, TRI_NONE>(o.CW.p, m2, n, o.CW.ld, o.py, EpiKF<TO>{q, Dw, p}, part_pq, skip, s); // a8
+    }
+
+    // ------------------------------------------------------------------- PCG
+    // One PCG iteration (a6-a10): K_F p, alpha update, preconditioner, beta update.
+    template <typename TO, typename TP>
+    void pcg_body(int kind) {
+        Op<TO>& o = op<TO>();
+        Pc<TP>& P = pcd<TP>();
+        const int* skip = &st->done;
+        const int npq = kf_apply_dev<TO>(o.pp, o.pq, o.pD, skip);
+        const int gv = vec_grid(m2);
+        if (kind == PC_L_K)
+            pcg_alpha_kernel<TO, TP, PC_L_K><<<gv, kVecThreads, 0, s>>>(m2, st, part_pq, npq, o.px, o.pr, o.pp, o.pq,
+                                                                         o.pz, o.pDinv, P.rs, P.sg, part_rr, part_rz);
+        else if (kind == PC_H_K)
+            pcg_alpha_kernel<TO, TP, PC_H_K><<<gv, kVecThreads, 0, s>>>(m2, st, part_pq, npq, o.px, o.pr, o.pp, o.pq,
+                                                                         o.pz, o.pDinv, P.rs, P.sg, part_rr, part_rz);
+        else
+            pcg_alpha_kernel<TO, TP, PC_NONE_K><<<gv, kVecThreads, 0, s>>>(m2, st, part_pq, npq, o.px, o.pr, o.pp, o.pq,
+                                                                            o.pz, o.pDinv, P.rs, P.sg, part_rr, part_rz);
+        int nrz = gv;
+        if (kind == PC_H_K) {                                                                          // a9
+            launch_gemv<TP, TRI_LOWER>(P.WPl.p, m2, m2, P.WPl.ld, P.rs, lin<TP>(P.pv), nullptr, skip, s);
+            nrz = launch_gemv<TP, TRI_UPPER>(P.WPu.p, m2, m2, P.WPu.ld, P.pv, EpiScaleDot<TP, TO>{o.pz, P.sg, o.pr},
+                                             part_rz, skip, s);
+        }
+        pcg_beta_kernel<TO><<<gv, kVecThreads, 0, s>>>(m2, st, o.pz, o.pp, part_rz, nrz, part_rr, gv);    // a10
+    }
+
+    template <typename TO, typename TP>
+    void pcg_init(int kind, const TO* rhs, double tol, int maxit, int stall) {
+        Op<TO>& o = op<TO>();
+        Pc<TP>& P = pcd<TP>();
+        const int gv = vec_grid(m2);
+        if (kind == PC_L_K)
+            pcg_init1_kernel<TO, TP, PC_L_K><<<gv, kVecThreads, 0, s>>>(m2, rhs, o.px, o.pr, o.pz, o.pDinv, P.rs, P.sg,
+                                                                         part_bb, part_rz);
+        else if (kind == PC_H_K)
+            pcg_init1_kernel<TO, TP, PC_H_K><<<gv, kVecThreads, 0, s>>>(m2, rhs, o.px, o.pr, o.pz, o.pDinv, P.rs, P.sg,
+                                                                         part_bb, part_rz);
+        else
+            pcg_init1_kernel<TO, TP, PC_NONE_K><<<gv, kVecThreads, 0, s>>>(m2, rhs, o.px, o.pr, o.pz, o.pDinv, P.rs,
+                                                                            P.sg, part_bb, part_rz);
+        int nrz = gv;
+        if (kind == PC_H_K) {
+            launch_gemv<TP, TRI_LOWER>(P.WPl.p, m2, m2, P.WPl.ld, P.rs, lin<TP>(P.pv), nullptr, nullptr, s);
+            nrz = launch_gemv<TP, TRI_UPPER>(P.WPu.p, m2, m2, P.WPu.ld, P.pv, EpiScaleDot<TP, TO>{o.pz, P.sg, o.pr},
+                                             part_rz, nullptr, s);
+        }
+        pcg_init2_kernel<TO><<<gv, kVecThreads, 0, s>>>(m2, st, o.pz, o.pp, part_bb, gv, part_rz, nrz, tol, maxit,
+                                                        stall);
+    }
+
+    int check_every() const { return opt.pcg_check_every > 0 ? opt.pcg_check_every : 8; }
+
+    // Iterations without a 4x residual decrease after which a Newton-direction
+    // solve stops: three times the exact-arithmetic bound of Corollaries 1/2
+    // (n-m1+1 for P_L, m1+1 for P_H; m2 without preconditioner) plus 100, so the
+    // plateau-then-drop convergence of CG on a few distinct eigenvalues is never cut.
+    int stall_window(int kind) const {
+        const int bound = kind == PC_L_K ? (n - m1 + 1) : (kind == PC_H_K ? (m1 + 1) : m2);
+        return 3 * bound + 100;
+    }
+
+    template <typename TO, typename TP>
+    cudaGraphExec_t get_graph(int kind) {
+        Op<TO>& o = op<TO>();
+        const int K = check_every();
+        if (o.graph[kind] && o.graph_k[kind] == K) return o.graph[kind];
+        if (o.graph[kind]) cudaGraphExecDestroy(o.graph[kind]);
+        cudaGraph_t g;
+        PCG_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        for (int i = 0; i < K; ++i) pcg_body<TO, TP>(kind);
+        PCG_CK(cudaStreamEndCapture(s, &g));
+        cudaGraphExec_t ge;
+        PCG_CK(cudaGraphInstantiate(&ge, g, 0));
+        cudaGraphDestroy(g);
+        o.graph[kind] = ge;
+        o.graph_k[kind] = K;
+        return ge;
+    }
+
+    // Runs PCG from the current pcg_init state until done (status checks are
+    // pipelined one graph launch behind); the final state ends in hst[0].
+    template <typename TO, typename TP>
+    void pcg_run(int kind, int maxit) {
+        cudaGraphExec_t ge = get_graph<TO, TP>(kind);
+        const int K = check_every();
+        const int max_launch = maxit / K + 2;
+        PCG_CK(cudaGraphLaunch(ge, s));
+        PCG_CK(cudaMemcpyAsync(&hst[0], st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+        PCG_CK(cudaEventRecord(ev0, s));
+        int launched = 1;
+        int cur = 0;
+        while (true) {
+            const bool second = launched < max_launch;
+            if (second) {
+                PCG_CK(cudaGraphLaunch(ge, s));
+                PCG_CK(cudaMemcpyAsync(&hst[1 - cur], st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+                PCG_CK(cudaEventRecord(cur == 0 ? ev1 : ev0, s));
+                ++launched;
+            }
+            PCG_CK(cudaEventSynchronize(cur == 0 ? ev0 : ev1));
+            if (hst[cur].done || !second) {
+                PCG_CK(cudaStreamSynchronize(s));
+                PCG_CK(cudaMemcpy(&hst[0], st, sizeof(PcgState), cudaMemcpyDeviceToHost));
+                break;
+            }
+            cur = 1 - cur;
+        }
+        PCG_CK(cudaGetLastError());
+    }
+
+    // D-dependent data of the operator precision TO (D and 1/D for P_L).
+    template <typename TO>
+    void set_D_op(const double* Dd) {
+        Op<TO>& o = op<TO>();
+        convert1d<double, TO>(m2, Dd, 1.0, o.pD, s);
+        recip_kernel<TO><<<vec_grid(m2), kVecThreads, 0, s>>>(m2, Dd, o.pDinv);
+    }
+
+    template <typename TP>
+    void set_D_pc(const double* Dd, int pc) {
+        if (pc_kind(pc) != PC_H_K) return;
+        ensure_T<TP>(pc);
+        PCG_CK(cudaEventRecord(evA, s));
+        build_ph<TP>(Dd);
+        PCG_CK(cudaEventRecord(evB, s));
+        PCG_CK(cudaEventSynchronize(evB));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, evA, evB);
+        stats.t_precond_ms += ms;
+    }
+
+    void set_D(const double* Dd, int pc) {
+        if (use64) set_D_op<double>(Dd); else set_D_op<float>(Dd);
+        if (f64) set_D_pc<double>(Dd, pc); else set_D_pc<float>(Dd, pc);
+    }
+
+    // PCG on K_F dnu = rhs with the operator of precision TO.
+    template <typename TO, typename TP>
+    int pcg_solve_t(const double* rhs, double* dnu, int kind, double tol, int maxit, int* iters, double* relres) {
+        Op<TO>& o = op<TO>();
+        convert1d<double, TO>(m2, rhs, 1.0, o.prhs, s);
+        pcg_init<TO, TP>(kind, o.prhs, tol, maxit, 0);
+        pcg_run<TO, TP>(kind, maxit);
+        convert1d<TO, double>(m2, o.px, 1.0, dnu, s);
+        sync_check();
+        if (iters) *iters = hst[0].iter;
+        if (relres) *relres = hst[0].bb > 0 ? std::sqrt(hst[0].rr / hst[0].bb) : 0.0;
+        if (hst[0].done == 3) return QP_ENUMERIC;
+        if (hst[0].done == 2) return QP_EMAXIT;
+        return QP_OK;
+    }
+
+    int pcg_solve(const double* Dd, const double* rhs, double* dnu, int pc, double tol, int maxit, int* iters,
+                  double* relres) {
+        pc = resolve_pc(pc, n, m1);
+        set_D(Dd, pc);
+        const int kind = pc_kind(pc);
+        if (use64) return f64 ? pcg_solve_t<double, double>(rhs, dnu, kind, tol, maxit, iters, relres)
+                              : pcg_solve_t<double, float>(rhs, dnu, kind, tol, maxit, iters, relres);
+        return pcg_solve_t<float, float>(rhs, dnu, kind, tol, maxit, iters, relres);
+    }
+
+    template <typename TO, typename TP>
+    void time_pcg_t(int kind, int warmup, int iters, double* ms_out) {
+        Op<TO>& o = op<TO>();
+        const int K = check_every();
+        cudaGraphExec_t ge = get_graph<TO, TP>(kind);
+        const int nw = (warmup + K - 1) / K, nt = std::max(1, (iters + K - 1) / K);
+        pcg_init<TO, TP>(kind, o.prhs, 0.0, (nw + nt) * K + 1, 0);
+        for (int i = 0; i < nw; ++i) PCG_CK(cudaGraphLaunch(ge, s));
+        PCG_CK(cudaMemcpyAsync(&hst[1], st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+        PCG_CK(cudaEventRecord(evA, s));
+        for (int i = 0; i < nt; ++i) PCG_CK(cudaGraphLaunch(ge, s));
+        PCG_CK(cudaEventRecord(evB, s));
+        PCG_CK(cudaMemcpyAsync(&hst[0], st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+        sync_check();
+        float ms = 0.f;
+        PCG_CK(cudaEventElapsedTime(&ms, evA, evB));
+        const int done_iters = hst[0].iter - hst[1].iter;
+        *ms_out = done_iters > 0 ? ms / done_iters : -1.0;
+    }
+
+    // Mean device time of one PCG iteration (rhs = D, tolerance 0: no early stop).
+    void time_pcg(const double* Dd, int pc, int warmup, int iters, double* ms_out) {
+        pc = resolve_pc(pc, n, m1);
+        set_D(Dd, pc);
+        const int kind = pc_kind(pc);
+        if (use64) {
+            convert1d<double, double>(m2, Dd, 1.0, o64.prhs, s);
+            if (f64) time_pcg_t<double, double>(kind, warmup, iters, ms_out);
+            else time_pcg_t<double, float>(kind, warmup, iters, ms_out);
+        } else {
+            convert1d<double, float>(m2, Dd, 1.0, o32.prhs, s);
+            time_pcg_t<float, float>(kind, warmup, iters, ms_out);
+        }
+    }
+
+    // Algorithmic bytes of one PCG iteration (the per-iteration traffic of
+    // Table tab:costs with dense operands): C' p and C y stream C twice; the K0
+    // solve streams the two triangles of R^{-1} and Gt twice; P_H streams the two
+    // triangles of its inverse factor; plus the vector traffic.
+    double bytes_per_iter(int pc) const {
+        pc = resolve_pc(pc, n, m1);
+        const double eo = use64 ? 8.0 : 4.0, ep = f64 ? 8.0 : 4.0;
+        const double bo = 2.0 * m2 * n + (double)n * (n + 1) + 2.0 * m1 * n;
+        const double bp = pc_kind(pc) == PC_H_K ? (double)m2 * (m2 + 1) : 0.0;
+        const double vec_el = 12.0 * m2 + 8.0 * n + 4.0 * m1;
+        return bo * eo + bp * ep + vec_el * eo;
+    }
+
+    void kf_apply(const double* Dd, const double* p, double* q) {
+        if (use64) kf_apply_t<double>(Dd, p, q); else kf_apply_t<float>(Dd, p, q);
+    }
+    template <typename TO>
+    void kf_apply_t(const double* Dd, const double* p, double* q) {
+        Op<TO>& o = op<TO>();
+        convert1d<double, TO>(m2, Dd, 1.0, o.pD, s);
+        convert1d<double, TO>(m2, p, 1.0, o.pp, s);
+        kf_apply_dev<TO>(o.pp, o.pq, o.pD, nullptr);
+        convert1d<TO, double>(m2, o.pq, 1.0, q, s);
+        sync_check();
+    }
+
+    void k0_solve(const double* u, const double* w, double* a, double* bout) {
+        if (use64) k0_solve_t<double>(u, w, a, bout); else k0_solve_t<float>(u, w, a, bout);
+    }
+    template <typename TO>
+    void k0_solve_t(const double* u, const double* w, double* a, double* bout) {
+        Op<TO>& o = op<TO>();
+        convert1d<double, TO>(n, u, 1.0, o.ku, s);
+        if (w && m1) convert1d<double, TO>(m1, w, 1.0, o.kw, s);
+        k0_solve_dev<TO>(o.ku, (w && m1) ? o.kw : nullptr, o.ka, m1 ? o.kmb : nullptr);
+        convert1d<TO, double>(n, o.ka, 1.0, a, s);
+        if (bout && m1) convert1d<TO, double>(m1, o.kmb, -1.0, bout, s);
+        sync_check();
+    }
+
+    // ------------------------------------------------- reduced Newton solve
+    // Solve K^{(k)} [dx; dlam; dnu] = [f_g; f_e; f_a] (eq. [augmented]) through the
+    // reduced system with the operator of precision TO:
+    //   K_F dnu = f_a - [C 0] K0^{-1} [-f_g; f_e]      (eq. [ineq-const-reduced], K0 form)
+    //   K0 [dx; -dlam] = [C' dnu - f_g; f_e]           (eq. [schur-delta-x], K0 form)
+    // Inputs and outputs FP64; the right-hand side is scaled to unit norm inside
+    // (the system is linear) so the working precision never under- or overflows.
+    template <typename TO, typename TP>
+    int reduced_solve_t(const double* gg, const double* ge_, const double* ga, double* ox, double* ol, double* on,
+                        int kind, double tol, int maxit, double rhs_norm) {
+        Op<TO>& o = op<TO>();
+        const double inv = 1.0 / rhs_norm;
+        convert1d<double, TO>(n, gg, -inv, o.ku, s);
+        if (m1) convert1d<double, TO>(m1, ge_, inv, o.kw, s);
+        k0_solve_dev<TO>(o.ku, m1 ? o.kw : nullptr, o.ka, nullptr);
+        convert1d<double, TO>(m2, ga, inv, o.wa, s);
+        launch_gemv<TO, TRI_NONE>(o.CW.p, m2, n, o.CW.ld, o.ka, EpiRnu<TO>{o.prhs, o.wa}, nullptr, nullptr, s);  // a5
+        PCG_CK(cudaEventRecord(evA, s));
+        pcg_init<TO, TP>(kind, o.prhs, tol, maxit, stall_window(kind));
+        pcg_run<TO, TP>(kind, maxit);
+        if (hst[0].done == 3 && kind != PC_L_K) {
+            // non-finite PCG with the factored preconditioner: redo this solve with P_L
+            if (verbose) std::fprintf(stderr, "    PCG non-finite with kind %d: retry with P_L\n", kind);
+            pcg_init<TO, TP>(PC_L_K, o.prhs, tol, maxit, stall_window(PC_L_K));
+            pcg_run<TO, TP>(PC_L_K, maxit);
+        }
+        PCG_CK(cudaEventRecord(evB, s));
+        // recovery (a11)
+        convert1d<double, TO>(n, gg, inv, o.wg, s);
+        launch_gemv<TO, TRI_NONE>(o.CWT.p, n, m2, o.CWT.ld, o.px, lin<TO>(o.ku, TO(1), o.wg, TO(-1)), nullptr, nullptr, s);
+        k0_solve_dev<TO>(o.ku, m1 ? o.kw : nullptr, o.ka, m1 ? o.kmb : nullptr);
+        convert1d<TO, double>(n, o.ka, rhs_norm, ox, s);
+        if (m1) convert1d<TO, double>(m1, o.kmb, rhs_norm, ol, s);
+        convert1d<TO, double>(m2, o.px, rhs_norm, on, s);
+        PCG_CK(cudaEventSynchronize(evB));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, evA, evB);
+        stats.t_pcg_ms += ms;
+        stats.newton_solves += 1;
+        if (std::is_same<TO, double>::value && !f64) stats.op64_solves += 1;
+        stats.pcg_iters_total += hst[0].iter;
+        last_pcg_done = hst[0].done;
+        last_pcg_rel = hst[0].bb > 0 ? std::sqrt(hst[0].rr / hst[0].bb) : 0.0;
+        if (hst[0].done == 3) return -1;
+        return hst[0].iter;
+    }
+
+    int reduced_solve(const double* gg, const double* ge_, const double* ga, double* ox, double* ol, double* on,
+                      int kind, double tol, int maxit, double rhs_norm) {
+        if (!(rhs_norm > 0.0)) {   // zero right-hand side: zero direction
+            axpby<double, double>(n, 0.0, gg, 0.0, ox, s);
+            if (m1) axpby<double, double>(m1, 0.0, ge_, 0.0, ol, s);
+            axpby<double, double>(m2, 0.0, ga, 0.0, on, s);
+            return 0;
+        }
+        if (use64) {
+            if (f64) return reduced_solve_t<double, double>(gg, ge_, ga, ox, ol, on, kind, tol, maxit, rhs_norm);
+            return reduced_solve_t<double, float>(gg, ge_, ga, ox, ol, on, kind, tol, maxit, rhs_norm);
+        }
+        return reduced_solve_t<float, float>(gg, ge_, ga, ox, ol, on, kind, tol, maxit, rhs_norm);
+    }
+
+    // rho = f - K^{(k)} z in FP64; returns |rho|_2^2 (eq. [augmented], D = s / nu).
+    double kkt3_residual(const double* zx, const double* zl, const double* zn) {
+        launch_gemv<double, TRI_NONE>(H.p, n, n, H.ld, zx, lin<double>(rho_g, 1.0, fg, 1.0), nullptr, nullptr, s);
+        if (m1) launch_gemv<double, TRI_NONE>(AT.p, n, m1, AT.ld, zl, lin<double>(rho_g, -1.0, rho_g, 1.0), nullptr, nullptr, s);
+        launch_gemv<double, TRI_NONE>(CT.p, n, m2, CT.ld, zn, lin<double>(rho_g, -1.0, rho_g, 1.0), nullptr, nullptr, s);
+        if (m1) launch_gemv<double, TRI_NONE>(A.p, m1, n, A.ld, zx, lin<double>(rho_e, -1.0, fe, 1.0), nullptr, nullptr, s);
+        launch_gemv<double, TRI_NONE>(C.p, m2, n, C.ld, zx,
+                                      lin<double>(rho_a, -1.0, fa, 1.0, nullptr, 0.0, D64, zn, -1.0), nullptr, nullptr, s);
+        return sumsq3(rho_g, rho_e, rho_a);
+    }
+
+    double sumsq3(const double* a, const double* bb, const double* cc) {
+        norms_kernel<<<vec_grid(n), kVecThreads, 0, s>>>(n, a, part_a, part_b);
+        if (m1) norms_kernel<<<vec_grid(m1), kVecThreads, 0, s>>>(m1, bb, part_c, part_b);
+        norms_kernel<<<vec_grid(m2), kVecThreads, 0, s>>>(m2, cc, part_d, part_b);
+        ReduceJob job{};
+        job.part[0] = part_a; job.cnt[0] = vec_grid(n); job.op[0] = 0;
+        job.part[1] = part_c; job.cnt[1] = m1 ? vec_grid(m1) : 0; job.op[1] = 0;
+        job.part[2] = part_d; job.cnt[2] = vec_grid(m2); job.op[2] = 0;
+        job.njobs = 3;
+        reduce_jobs_kernel<<<1, kVecThreads, 0, s>>>(job, d_scal);
+        PCG_CK(cudaMemcpyAsync(h_scal, d_scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        PCG_CK(cudaStreamSynchronize(s));
+        return h_scal[0] + (m1 ? h_scal[1] : 0.0) + h_scal[2];
+    }
+
+    // Move the operator to FP64 for the rest of the QP (mixed precision mode).
+    void switch_to_op64() {
+        if (use64) return;
+        factor_op<double>();
+        use64 = true;
+        set_D_op<double>(D64);
+        stats.op64_switch_iter = ipm_k;
+        if (verbose) std::fprintf(stderr, "  operator -> FP64 at IPM iteration %d\n", ipm_k);
+    }
+
+    // Newton direction for the rhs (fg, fe, fa) already in place; result in (ox, ol, on).
+    // PARITY mode refines against the FP64 residual of the 3x3 system.  With the FP32
+    // operator a sweep contracts by about max(PCG tolerance, operator error); the next
+    // corrections are then solved only to half that contraction, and a contraction
+    // worse than 1/4 (or a correction that increases the residual) moves the QP to the
+    // FP64 operator.
+    int newton_solve(double* ox, double* ol, double* on, int kind) {
+        const bool paper = (opt.pcg_mode == QP_MODE_PAPER);
+        const int maxit = opt.max_pcg > 0 ? opt.max_pcg : 4 * m2 + 50;
+        auto base_tol = [&]() {
+            double t = opt.pcg_tol;
+            if (t <= 0) t = paper ? 1e-3 : (use64 ? 1e-10 : 1e-6);
+            return t;
+        };
+        const double fnorm2 = sumsq3(fg, fe, fa);
+        int it = reduced_solve(fg, fe, fa, ox, ol, on, kind, base_tol(), maxit, std::sqrt(fnorm2));
+        if (verbose) std::fprintf(stderr, "    solve: |f|=%.3e pcg=%d done=%d rel=%.2e op64=%d\n", std::sqrt(fnorm2),
+                                  it, last_pcg_done, last_pcg_rel, (int)use64);
+        if (it < 0) return QP_ENUMERIC;
+        if (paper) return QP_OK;
+        double prev = kkt3_residual(ox, ol, on);
+        const double rtol2 = opt.refine_tol * opt.refine_tol * fnorm2;
+        if (verbose) std::fprintf(stderr, "      refine 0: |rho|/|f|=%.3e\n", std::sqrt(prev / fnorm2));
+        double last = fnorm2;
+        int budget = opt.refine_max;
+        for (int sweep = 0; sweep < budget && prev > rtol2; ++sweep) {
+            const double contraction = std::sqrt(prev / last);
+            if (!use64 && sweep > 0 && contraction > 0.25) {
+                switch_to_op64();
+                budget = sweep + opt.refine_max;   // fresh sweeps with the FP64 operator
+            }
+            double ctol = base_tol();
+            if (!use64 && opt.pcg_tol <= 0) ctol = std::min(1e-1, std::max(ctol, 0.5 * contraction));
+            last = prev;
+            it = reduced_solve(rho_g, rho_e, rho_a, tx, tl, tn, kind, ctol, maxit, std::sqrt(prev));
+            if (it < 0) return QP_ENUMERIC;
+            axpby<double, double>(n, 1.0, tx, 1.0, ox, s);
+            if (m1) axpby<double, double>(m1, 1.0, tl, 1.0, ol, s);
+            axpby<double, double>(m2, 1.0, tn, 1.0, on, s);
+            stats.refine_sweeps += 1;
+            const double r2 = kkt3_residual(ox, ol, on);
+            if (verbose) std::fprintf(stderr, "      refine %d: pcg=%d done=%d rel=%.2e |rho|/|f|=%.3e op64=%d\n",
+                                      sweep + 1, it, last_pcg_done, last_pcg_rel, std::sqrt(r2 / fnorm2), (int)use64);
+            if (r2 > prev) {
+                // the correction made it worse: undo it; with the FP32 operator move to FP64
+                axpby<double, double>(n, -1.0, tx, 1.0, ox, s);
+                if (m1) axpby<double, double>(m1, -1.0, tl, 1.0, ol, s);
+                axpby<double, double>(m2, -1.0, tn, 1.0, on, s);
+                if (use64) break;
+                kkt3_residual(ox, ol, on);     // restore rho for the next correction
+                switch_to_op64();
+                budget = sweep + 1 + opt.refine_max;
+                last = prev;
+                continue;
+            }
+            prev = r2;
+        }
+        return QP_OK;
+    }
+
+    // -------------------------------------------------------------------- IPM
+    // |r_g|_inf, |r_e|_inf, |r_i|_inf, s'nu, x'Hx, c'x at the current iterate.
+    void residuals(double* out6) {
+        launch_gemv<double, TRI_NONE>(H.p, n, n, H.ld, x, lin<double>(hx), nullptr, nullptr, s);
+        // r_g = -Hx - c + A'lam + C'nu ; r_e = Ax - b ; r_i = Cx - d - s  (eq. [rhs-KKT4])
+        launch_gemv<double, TRI_NONE>(CT.p, n, m2, CT.ld, nu, lin<double>(rg, 1.0, hx, -1.0, c, -1.0), nullptr, nullptr, s);
+        if (m1) launch_gemv<double, TRI_NONE>(AT.p, n, m1, AT.ld, lam, lin<double>(rg, 1.0, rg, 1.0), nullptr, nullptr, s);
+        if (m1) launch_gemv<double, TRI_NONE>(A.p, m1, n, A.ld, x, lin<double>(re, 1.0, b, -1.0), nullptr, nullptr, s);
+        launch_gemv<double, TRI_NONE>(C.p, m2, n, C.ld, x, lin<double>(ri, 1.0, d, -1.0, sl, -1.0), nullptr, nullptr, s);
+        norms_kernel<<<vec_grid(n), kVecThreads, 0, s>>>(n, rg, part_a, part_b);
+        if (m1) norms_kernel<<<vec_grid(m1), kVecThreads, 0, s>>>(m1, re, part_a, part_c);
+        norms_kernel<<<vec_grid(m2), kVecThreads, 0, s>>>(m2, ri, part_a, part_d);
+        dot_kernel<<<vec_grid(m2), kVecThreads, 0, s>>>(m2, sl, nu, part_e);
+        dot_kernel<<<vec_grid(n), kVecThreads, 0, s>>>(n, x, hx, part_f);
+        dot_kernel<<<vec_grid(n), kVecThreads, 0, s>>>(n, x, c, part_bb);
+        ReduceJob job{};
+        job.part[0] = part_b; job.cnt[0] = vec_grid(n); job.op[0] = 1;
+        job.part[1] = part_c; job.cnt[1] = m1 ? vec_grid(m1) : 0; job.op[1] = 1;
+        job.part[2] = part_d; job.cnt[2] = vec_grid(m2); job.op[2] = 1;
+        job.part[3] = part_e; job.cnt[3] = vec_grid(m2); job.op[3] = 0;
+        job.part[4] = part_f; job.cnt[4] = vec_grid(n); job.op[4] = 0;
+        job.part[5] = part_bb; job.cnt[5] = vec_grid(n); job.op[5] = 0;
+        job.njobs = 6;
+        reduce_jobs_kernel<<<1, kVecThreads, 0, s>>>(job, d_scal);
+        PCG_CK(cudaMemcpyAsync(h_scal, d_scal, 6 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        sync_check();
+        for (int k = 0; k < 6; ++k) out6[k] = h_scal[k];
+        if (!m1) out6[1] = 0.0;
+    }
+
+    double reduce1(const double* part, int cnt, int opk) {
+        ReduceJob job{};
+        job.part[0] = part; job.cnt[0] = cnt; job.op[0] = opk; job.njobs = 1;
+        reduce_jobs_kernel<<<1, kVecThreads, 0, s>>>(job, d_scal);
+        PCG_CK(cudaMemcpyAsync(h_scal, d_scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+        sync_check();
+        return h_scal[0];
+    }
+
+    double max_step(const double* s_, const double* ds_, const double* nu_, const double* dnu_) {
+        ipm_maxstep_kernel<<<vec_grid(m2), kVecThreads, 0, s>>>(m2, s_, ds_, nu_, dnu_, part_a);
+        return reduce1(part_a, vec_grid(m2), 2);
+    }
+
+    double mu_aff(double a) {
+        ipm_muaff_kernel<<<vec_grid(m2), kVecThreads, 0, s>>>(m2, sl, dsa, nu, dna, a, part_a);
+        return reduce1(part_a, vec_grid(m2), 0) / m2;
+    }
+
+    // Start point: K0 [x; -lam] = [-c; b] refined in FP64, s = max(Cx - d, 1), nu = 1.
+    template <typename TO>
+    void start_point_t() {
+        Op<TO>& o = op<TO>();
+        constexpr bool is64 = std::is_same<TO, double>::value;
+        convert1d<double, TO>(n, c, -1.0, o.ku, s);
+        if (m1) convert1d<double, TO>(m1, b, 1.0, o.kw, s);
+        k0_solve_dev<TO>(o.ku, m1 ? o.kw : nullptr, o.ka, m1 ? o.kmb : nullptr);
+        convert1d<TO, double>(n, o.ka, 1.0, x, s);
+        if (m1) convert1d<TO, double>(m1, o.kmb, 1.0, lam, s);
+        for (int sweep = 0; sweep < (is64 ? 2 : 6); ++sweep) {
+            // rho1 = -c - H x + A' lam ; rho2 = b - A x ; K0 [dx; -dlam] = [rho1; rho2]
+            launch_gemv<double, TRI_NONE>(H.p, n, n, H.ld, x, lin<double>(rho_g, -1.0, c, -1.0), nullptr, nullptr, s);
+            if (m1) {
+                launch_gemv<double, TRI_NONE>(AT.p, n, m1, AT.ld, lam, lin<double>(rho_g, 1.0, rho_g, 1.0), nullptr, nullptr, s);
+                launch_gemv<double, TRI_NONE>(A.p, m1, n, A.ld, x, lin<double>(rho_e, -1.0, b, 1.0), nullptr, nullptr, s);
+                convert1d<double, TO>(m1, rho_e, 1.0, o.kw, s);
+            }
+            convert1d<double, TO>(n, rho_g, 1.0, o.ku, s);
+            k0_solve_dev<TO>(o.ku, m1 ? o.kw : nullptr, o.ka, m1 ? o.kmb : nullptr);
+            convert1d<TO, double>(n, o.ka, 1.0, tx, s);
+            axpby<double, double>(n, 1.0, tx, 1.0, x, s);
+            if (m1) {
+                convert1d<TO, double>(m1, o.kmb, 1.0, tl, s);
+                axpby<double, double>(m1, 1.0, tl, 1.0, lam, s);
+            }
+        }
+        launch_gemv<double, TRI_NONE>(C.p, m2, n, C.ld, x, lin<double>(ri, 1.0, d, -1.0), nullptr, nullptr, s);
+        ipm_start_kernel<<<vec_grid(m2), kVecThreads, 0, s>>>(m2, ri, sl, nu);
+    }
+
+    int ipm_solve() {
+        factor();
+        const auto t0 = std::chrono::steady_clock::now();
+        stats.ipm_iters = 0; stats.pcg_iters_total = 0; stats.newton_solves = 0; stats.refine_sweeps = 0;
+        stats.t_pcg_ms = 0; stats.t_precond_ms = 0; stats.op64_solves = 0; stats.op64_switch_iter = -1;
+        use64 = f64;
+        ipm_k = 0;
+        const int pc = resolve_pc(opt.precond, n, m1);
+        stats.precond_used = pc;
+        const int kind = pc_kind(pc);
+        if (use64) start_point_t<double>(); else start_point_t<float>();
+        int status = QP_EMAXIT;
+        int k = 0;
+        const double tau = 0.995;
+        while (true) {
+            double r6[6];
+            residuals(r6);
+            const double res_p = std::max(r6[1] / (1.0 + b_inf), r6[2] / (1.0 + d_inf));
+            const double res_d = r6[0] / (1.0 + c_inf + h_norm_inf);
+            const double mu = r6[3] / m2;
+            const double f = 0.5 * r6[4] + r6[5];
+            stats.res_p = res_p; stats.res_d = res_d; stats.mu = mu; stats.obj = f;
+            if (!std::isfinite(res_p) || !std::isfinite(res_d) || !std::isfinite(mu)) { status = QP_ENUMERIC; break; }
+            if (res_p <= opt.tol_feas && res_d <= opt.tol_feas && mu <= opt.tol_mu * (1.0 + std::fabs(f))) {
+                status = QP_OK;
+                break;
+            }
+            if (k >= opt.max_ipm) break;
+            ipm_k = k;
+            // D = V^{-1}S, predictor r_c = S V e, r_a = r_i + V^{-1} r_c
+            ipm_rc_kernel<<<vec_grid(m2), kVecThreads, 0, s>>>(m2, sl, nu, ri, nullptr, nullptr, 0.0, rc, ra, D64);
+            set_D(D64, pc);
+            // right-hand side of eq. [augmented]: -(r_g, r_e, r_a)
+            axpby<double, double>(n, -1.0, rg, 0.0, fg, s);
+            if (m1) axpby<double, double>(m1, -1.0, re, 0.0, fe, s);
+            axpby<double, double>(m2, -1.0, ra, 0.0, fa, s);
+            int st_ = newton_solve(dxa, dla, dna, kind);
+            if (st_ != QP_OK) { status = st_; break; }
+            ipm_ds_kernel<<<vec_grid(m2), kVecThreads, 0, s>>>(m2, rc, nu, D64, dna, dsa);
+            const double a_aff = std::min(1.0, max_step(sl, dsa, nu, dna));
+            const double mua = mu_aff(a_aff);
+            const double sigma = std::pow(mua / mu, 3.0);
+            // corrector: r_c = S V e + dS_aff dV_aff e - sigma mu e
+            ipm_rc_kernel<<<vec_grid(m2), kVecThreads, 0, s>>>(m2, sl, nu, ri, dsa, dna, sigma * mu, rc, ra, nullptr);
+            axpby<double, double>(m2, -1.0, ra, 0.0, fa, s);
+            st_ = newton_solve(dx, dl, dn, kind);
+            if (st_ != QP_OK) { status = st_; break; }
+            ipm_ds_kernel<<<vec_grid(m2), kVecThreads, 0, s>>>(m2, rc, nu, D64, dn, ds);
+            const double alpha = std::min(1.0, tau * max_step(sl, ds, nu, dn));
+            if (verbose)
+                std::fprintf(stderr, "ipm %d: mu=%.3e res_p=%.3e res_d=%.3e f=%.10g a_aff=%.3e sigma=%.3e alpha=%.3e\n",
+                             k, mu, res_p, res_d, f, a_aff, sigma, alpha);
+            axpby<double, double>(n, alpha, dx, 1.0, x, s);
+            if (m1) axpby<double, double>(m1, alpha, dl, 1.0, lam, s);
+            axpby<double, double>(m2, alpha, dn, 1.0, nu, s);
+            axpby<double, double>(m2, alpha, ds, 1.0, sl, s);
+            ++k;
+        }
+        sync_check();
+        stats.ipm_iters = k;
+        stats.status = status;
+        stats.t_solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        return status;
+    }
+
+    void copy_solution(double* xo, double* lo, double* no, double* so, bool to_host) {
+        const cudaMemcpyKind kd = to_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+        if (xo) PCG_CK(cudaMemcpyAsync(xo, x, (size_t)n * 8, kd, s));
+        if (lo && m1) PCG_CK(cudaMemcpyAsync(lo, lam, (size_t)m1 * 8, kd, s));
+        if (no) PCG_CK(cudaMemcpyAsync(no, nu, (size_t)m2 * 8, kd, s));
+        if (so) PCG_CK(cudaMemcpyAsync(so, sl, (size_t)m2 * 8, kd, s));
+        PCG_CK(cudaStreamSynchronize(s));
+    }
+};
+
+}  // namespace pcgipm

@@ -1,0 +1,255 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances
+----------
+FP64 working precision: the stored inverse triangular factors reproduce K0^{-1}
+to ~kappa(K0) u64 (u64 = 1.1e-16); the small cases here have kappa(K0) <= 1e6,
+so products match to 1e-9 relative and PCG (tol 1e-12) to 1e-8.
+FP32 working precision: u32 = 6e-8 and the inverse factor R^{-1} carries
+~kappa(R) u32 sqrt(n) relative error (kappa(R) = 1e2 here): products match to
+2e-3 relative in the 2-norm.
+IPM: relative objective error 1e-6 and scaled residuals 1e-8 (the acceptance
+bar), IPM iteration count within 2 of the oracle's.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import qpgen
+from oracle import bruteforce, ipm, reduced
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2104_12916_gb300 import binding, build
+    build.build()
+    binding.load()
+    return binding
+
+
+def _opts(B, prec, pc=0, **kw):
+    o = B.qp_opts_default()
+    o.precision = prec
+    o.precond = pc
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+TOL = {0: 1e-9, 1: 2e-3}       # keyed by precision enum (0 FP64, 1 FP32)
+SHAPES = [(120, 30, 200), (37, 5, 61), (130, 70, 150), (64, 0, 96), (5, 2, 7)]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_k0_solve(B, prec, shape):
+    n, m1, m2 = shape
+    q = qpgen.dense_qp(n, m1, m2, seed=11 + n)
+    h = B.QP.from_qpgen(q, _opts(B, prec)).factor()
+    rng = np.random.default_rng(1)
+    u, w = rng.standard_normal(n), rng.standard_normal(m1)
+    a, bo = np.zeros(n), np.zeros(m1)
+    B.qp_k0_solve(h.h, u, w if m1 else None, a, bo if m1 else None)
+    ref = np.linalg.solve(ipm.k0_matrix(q.H, q.A), np.concatenate([u, w]))
+    assert _rel(a, ref[:n]) <= TOL[prec]
+    if m1:
+        assert _rel(bo, ref[n:]) <= 5 * TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_kf_apply(B, prec, shape):
+    """q = K_F p elementwise against the oracle's three-step product."""
+    n, m1, m2 = shape
+    q = qpgen.dense_qp(n, m1, m2, seed=21 + n)
+    D, _ = qpgen.pcg_inputs(m2, 3)
+    h = B.QP.from_qpgen(q, _opts(B, prec)).factor()
+    p = np.random.default_rng(2).standard_normal(m2)
+    out = np.zeros(m2)
+    B.qp_kf_apply(h.h, D, p, out)
+    ref = reduced.kf_apply(q.H, q.A, q.C, D, p)
+    assert _rel(out, ref) <= TOL[prec]
+    assert np.max(np.abs(out - ref)) <= 10 * TOL[prec] * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("pc", [1, 2, 3, 4])
+def test_pcg_reduced_solve(B, prec, pc):
+    """K_F dnu = rhs: GPU PCG vs the direct solve of the explicit K_F, and the
+    GPU iteration count vs the oracle's textbook PCG (FP64)."""
+    n, m1, m2 = 60, 20, 150
+    q = qpgen.dense_qp(n, m1, m2, seed=31)
+    D, rhs = qpgen.pcg_inputs(m2, 5, 0.1, 10.0)
+    h = B.QP.from_qpgen(q, _opts(B, prec)).factor()
+    tol = 1e-12 if prec == 0 else 1e-5
+    dnu = np.zeros(m2)
+    st, it, rel = B.qp_pcg_reduced_solve(h.h, D, rhs, dnu, precond=pc, tol=tol, maxit=5000)
+    K = reduced.kf_explicit(q.H, q.A, q.C, D)
+    ref = np.linalg.solve(K, rhs)
+    assert rel <= tol
+    kap = np.linalg.cond(K)
+    assert _rel(dnu, ref) <= (1e-8 if prec == 0 else 2e-3), (it, kap)
+    if prec == 0:
+        if pc == 1:
+            Minv = lambda r: r / D
+        elif pc == 2:
+            P = reduced.P_H(q.H, q.C, D, exact=True)
+            Minv = lambda r: np.linalg.solve(P, r)
+        elif pc == 3:
+            P = reduced.P_H(q.H, q.C, D, exact=False)
+            Minv = lambda r: np.linalg.solve(P, r)
+        else:
+            Minv = lambda r: r
+        _, it_ref, _ = reduced.pcg(lambda v: K @ v, Minv, rhs, tol, 5000)
+        assert abs(it - it_ref) <= max(2, it_ref // 20), (it, it_ref)
+
+
+def test_pcg_corollary_bounds_on_gpu(B):
+    """Corollaries 1 and 2 hold for the GPU PCG in FP64 (one extra iteration of
+    slack for rounding, as in the oracle pin)."""
+    q = qpgen.dense_qp(40, 34, 90, seed=41)
+    D, rhs = qpgen.pcg_inputs(90, 6, 0.5, 2.0)
+    h = B.QP.from_qpgen(q, _opts(B, 0)).factor()
+    st, it, rel = B.qp_pcg_reduced_solve(h.h, D, rhs, np.zeros(90), precond=1, tol=1e-6, maxit=500)
+    assert it <= (40 - 34) + 2
+    q = qpgen.dense_qp(40, 3, 90, seed=42)
+    h = B.QP.from_qpgen(q, _opts(B, 0)).factor()
+    st, it, rel = B.qp_pcg_reduced_solve(h.h, D, rhs, np.zeros(90), precond=2, tol=1e-6, maxit=500)
+    assert it <= 3 + 2
+
+
+def _oracle_config0():
+    path = os.path.join(HERE, "golden", "oracle_config0.json")
+    with open(path) as fh:
+        return json.load(fh)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_ipm_config0(B, prec):
+    """Dense QP n=120, m1=30, m2=200 (seed 0): full IPM on the GPU vs the oracle."""
+    q = qpgen.config_qp(0)
+    gold = _oracle_config0()
+    xg = np.load(os.path.join(HERE, "golden", "oracle_config0_x.npy"))
+    h = B.QP.from_qpgen(q, _opts(B, prec))
+    x, lam, nu, s = np.zeros(q.n), np.zeros(q.m1), np.zeros(q.m2), np.zeros(q.m2)
+    st, f, its, pcg_its = B.qp_ipm_solve(h.h, x, lam, nu, s)
+    stats = B.qp_get_stats(h.h)
+    assert abs(f - gold["f"]) / max(abs(gold["f"]), 1.0) <= 1e-6
+    assert abs(its - gold["ipm_iters"]) <= 2, (its, gold["ipm_iters"])
+    assert stats["res_p"] <= 1e-8 and stats["res_d"] <= 1e-8
+    assert _rel(x, xg) <= 1e-6
+    rep = ipm.kkt_report(q.H, q.c, q.A, q.b, q.C, q.d, x, lam, nu, s)
+    assert rep["res_p"] <= 1e-8 and rep["res_d"] <= 1e-8 and rep["min_s"] > 0 and rep["min_nu"] > 0
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("pc", [1, 2, 3, 4])
+def test_ipm_every_preconditioner(B, prec, pc):
+    """The optimum does not depend on the preconditioner (it only changes PCG counts).
+
+    Unpreconditioned CG (U-KF) cannot resolve K_F to FP64 accuracy once D spans
+    many decades late in the IPM, so that variant is run to looser IPM tolerances
+    (1e-6 feasibility, mu <= 1e-8 (1+|f|)) and checked at the matching accuracy."""
+    q = qpgen.dense_qp(50, 12, 80, seed=7)
+    r = ipm.solve_qp(q)
+    kw = dict(tol_feas=1e-6, tol_mu=1e-8) if pc == 4 else {}
+    h = B.QP.from_qpgen(q, _opts(B, prec, pc, **kw))
+    x = np.zeros(q.n)
+    st, f, its, _ = B.qp_ipm_solve(h.h, x)
+    if pc == 4:
+        assert abs(f - r.f) / max(abs(r.f), 1.0) <= 1e-6
+        return
+    assert abs(f - r.f) / max(abs(r.f), 1.0) <= 1e-6
+    assert abs(its - r.iters) <= 2
+    assert _rel(x, r.x) <= 1e-5
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_ipm_tiny_vs_enumeration(B, seed):
+    """Tiny QPs (n <= 6): the GPU optimum equals the enumerated exact optimum."""
+    q = qpgen.tiny_qp(seed)
+    bf = bruteforce.bruteforce(q.H, q.c, q.A, q.b, q.C, q.d)
+    for prec in (0, 1):
+        h = B.QP.from_qpgen(q, _opts(B, prec))
+        x = np.zeros(q.n)
+        st, f, its, _ = B.qp_ipm_solve(h.h, x)
+        assert abs(f - bf["f"]) / max(1.0, abs(bf["f"])) <= 1e-8
+        assert np.linalg.norm(x - bf["x"]) <= 1e-6 * max(1.0, np.linalg.norm(bf["x"]))
+
+
+def test_ipm_no_equality_constraints(B):
+    """m1 = 0 (K0 = H): the library accepts it and reaches the oracle's optimum."""
+    q = qpgen.dense_qp(40, 0, 70, seed=9)
+    r = ipm.solve_qp(q)
+    h = B.QP.from_qpgen(q, _opts(B, 1))
+    st, f, its, _ = B.qp_ipm_solve(h.h)
+    assert abs(f - r.f) / max(abs(r.f), 1.0) <= 1e-6
+
+
+def test_deterministic(B):
+    """Fixed reduction trees: two solves give bit-identical results."""
+    q = qpgen.dense_qp(70, 20, 110, seed=12)
+    out = []
+    for _ in range(2):
+        h = B.QP.from_qpgen(q, _opts(B, 1))
+        x = np.zeros(q.n)
+        B.qp_ipm_solve(h.h, x)
+        out.append(x.copy())
+    assert np.array_equal(out[0], out[1])
+
+
+def test_error_paths(B):
+    q = qpgen.dense_qp(20, 5, 30, seed=3)
+    # indefinite H -> not convex (checked at the FP64 pivots of chol(H))
+    Hbad = q.H - 2.0 * np.max(np.linalg.eigvalsh(q.H)) * np.eye(20)
+    h = B.QP(Hbad, q.c, q.A, q.b, q.C, q.d, _opts(B, 1))
+    with pytest.raises(B.QPError) as e:
+        h.factor()
+    assert e.value.status == B.QP_ENOTCONVEX
+    # rank-deficient A -> singular F_H
+    Abad = q.A.copy()
+    Abad[1] = Abad[0]
+    h = B.QP(q.H, q.c, Abad, q.b, q.C, q.d, _opts(B, 0))
+    with pytest.raises(B.QPError) as e:
+        h.factor()
+    assert e.value.status == B.QP_ESINGULAR
+    # NaN input and asymmetric H are rejected at create
+    Hn = q.H.copy()
+    Hn[3, 4] = np.nan
+    with pytest.raises(B.QPError) as e:
+        B.QP(Hn, q.c, q.A, q.b, q.C, q.d)
+    assert e.value.status == B.QP_EINVAL
+    Ha = q.H.copy()
+    Ha[3, 4] += 1e-3
+    with pytest.raises(B.QPError) as e:
+        B.QP(Ha, q.c, q.A, q.b, q.C, q.d)
+    assert e.value.status == B.QP_EINVAL
+    # solve before factor is refused for the hot-path entry points
+    h = B.QP.from_qpgen(q)
+    with pytest.raises(B.QPError) as e:
+        B.qp_kf_apply(h.h, np.ones(30), np.ones(30), np.zeros(30))
+    assert e.value.status == B.QP_ESTATE
+
+
+def test_device_pointers(B):
+    """ptr_kind = DEVICE: torch CUDA float64 tensors in and out give the same result."""
+    torch = pytest.importorskip("torch")
+    q = qpgen.dense_qp(60, 10, 90, seed=13)
+    hh = B.QP.from_qpgen(q, _opts(B, 1))
+    xh = np.zeros(q.n)
+    B.qp_ipm_solve(hh.h, xh)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    hd = B.QP(t(q.H), t(q.c), t(q.A), t(q.b), t(q.C), t(q.d), _opts(B, 1))
+    xd = torch.zeros(q.n, dtype=torch.float64, device="cuda")
+    B.qp_ipm_solve(hd.h, xd)
+    assert np.array_equal(xd.cpu().numpy(), xh)
