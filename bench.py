@@ -1,0 +1,358 @@
+#!/usr/bin/env python3
+"""Benchmark: QPs solved per second on the dense few-equalities QP
+(n=2000, m_eq=200, m_in=4000, seed 1), mixed precision vs plain FP64.
+
+A step is one whole solve through the C ABI: qp_create from inputs resident in
+HBM (device-to-device copy), qp_factor_K0 (the setup phase), qp_ipm_solve (all
+IPM iterations with their reduced PCG solves), qp_destroy.  A step counts as a
+solved QP when its objective is within 1e-6 (relative) of the FP64 oracle's.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun, one process per GPU) every rank solves its own replica of
+the QP: the method has no data-parallel exchange for a single QP.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import qpgen  # noqa: E402
+
+WORKLOAD = "dense convex QP n=2000 m_eq=200 m_in=4000 (Lambda log-uniform [1e-3,1e3], seed 1)"
+METRIC = "QPs solved/s at 1e-6 obj err (mixed precision; FP64 path alongside)"
+CONFIG_ID = 1
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=1, help="timed steps of the FP64 comparison line")
+    ap.add_argument("--profile-pcg", type=int, default=0, metavar="ITERS",
+                    help="only factor the QP and run ITERS PCG iterations (a short run for ncu)")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"], help="precision of --profile-pcg")
+    return ap.parse_args()
+
+
+def golden():
+    with open(os.path.join(ROOT, "tests", "golden", f"oracle_config{CONFIG_ID}.json")) as fh:
+        return json.load(fh)
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ---------------------------------------------------------------- CPU baseline
+def oracle_sample(qp, ipm_iters_full, sample_iters=2):
+    """Time the FP64 oracle (3x3 LDL^T variant) on a bounded sample of the same
+    workload: its setup plus `sample_iters` IPM iterations, scaled to a full solve
+    by the oracle's own iteration count."""
+    from oracle import ipm
+    t0 = time.perf_counter()
+    ipm.start_point(qp.H, qp.c, qp.A, qp.b, qp.C, qp.d)
+    t_setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ipm.solve_qp(qp, variant="kkt3", max_ipm=sample_iters)
+    t_iters = time.perf_counter() - t0 - t_setup
+    per_iter = t_iters / sample_iters
+    t_full = t_setup + per_iter * ipm_iters_full
+    cores = len(os.sched_getaffinity(0))
+    return dict(value=1.0 / t_full, unit="QPs/s", cores=cores, kind="oracle",
+                sample=f"start point + {sample_iters} of {ipm_iters_full} IPM iterations of the FP64 "
+                       f"3x3-LDL^T oracle on the same QP, scaled to the full solve "
+                       f"({per_iter:.2f} s/iteration, {t_full:.1f} s/QP)")
+
+
+# ---------------------------------------------------------------------- clocks
+REASONS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap", 0x8: "hw_slowdown",
+           0x10: "sync_boost", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+           0x80: "hw_power_brake_slowdown", 0x100: "display_clock_setting"}
+
+
+class ClockSampler:
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=clocks.sm,clocks.max.sm,clocks_event_reasons.active",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 3:
+                try:
+                    self.samples.append((float(parts[0]), float(parts[1]), int(parts[2], 16)))
+                except ValueError:
+                    pass
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        mask = 0
+        for _, _, m in self.samples:
+            mask |= m
+        return {"sm_mhz": statistics.median(s[0] for s in self.samples),
+                "sm_max_mhz": max(s[1] for s in self.samples),
+                "reasons": [name for bit, name in REASONS.items() if mask & bit],
+                "samples": len(self.samples)}
+
+
+# ------------------------------------------------------------------ our solver
+def run_ours(args):
+    import torch
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2104_12916_gb300 import binding as B, build
+    build.build()
+    B.load()
+    gold = golden()
+    qp = qpgen.config_qp(CONFIG_ID)
+    dev = torch.device("cuda", local)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    Hd, cd, Ad, bd, Cd, dd = t(qp.H), t(qp.c), t(qp.A), t(qp.b), t(qp.C), t(qp.d)
+    xd = torch.zeros(qp.n, dtype=torch.float64, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > 129 MB L2
+    # The solver runs on this (non-default) stream: PCG graphs are captured on it and
+    # the CUDA events below are recorded on it.
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.synchronize()
+    torch.cuda.set_stream(stream)
+
+    def opts(prec):
+        o = B.qp_opts_default()
+        o.precision = prec
+        o.stream = stream.cuda_stream
+        return o
+
+    def step(prec, out):
+        h = B.qp_create(Hd, cd, Ad, bd, Cd, dd, opts(prec))
+        try:
+            st, f, its, pits = B.qp_ipm_solve(h, xd, allow=(B.QP_OK, B.QP_EMAXIT, B.QP_ENUMERIC))
+            out.append(dict(status=st, f=f, ipm=its, pcg=pits, stats=B.qp_get_stats(h)))
+        finally:
+            B.qp_destroy(h)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(prec, steps, warmup):
+        res = []
+        for _ in range(warmup):
+            step(prec, [])
+        barrier()
+        total_ms = 0.0
+        l0 = B.qp_kernel_launches()
+        for _ in range(steps):
+            flush.fill_(1.0)                     # evict L2 between timed steps (not timed)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(prec, res)
+            e1.record(stream)
+            e1.synchronize()
+            total_ms += e0.elapsed_time(e1)
+        barrier()
+        launches = B.qp_kernel_launches() - l0
+        if world > 1:
+            import torch.distributed as dist
+            tt = torch.tensor([total_ms], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            total_ms = float(tt.item())
+        ok = [abs(r["f"] - gold["f"]) / max(abs(gold["f"]), 1.0) <= 1e-6 and r["status"] == 0 for r in res]
+        return res, total_ms, ok, launches
+
+    with ClockSampler(local) as clk:
+        res, total_ms, ok, launches = timed(B.QP_PREC_FP32, args.steps, args.warmup)
+    res64, total64, ok64, _ = timed(B.QP_PREC_FP64, args.fp64_steps, 1)
+
+    solved = sum(ok) * world
+    value = solved / (total_ms / 1e3)
+    value64 = sum(ok64) * world / (total64 / 1e3)
+
+    # ---- roofline of the dominant kernel chain: one PCG iteration (a6-a10)
+    o = opts(B.QP_PREC_FP32)
+    h = B.qp_create(Hd, cd, Ad, bd, Cd, dd, o)
+    B.qp_factor_K0(h)
+    # an early-IPM D (s, nu of order one): the FP32 P_H factor applies, so this times
+    # the FP32 hot path (the bytes and work per iteration do not depend on D's values)
+    Dmid = np.exp(np.random.default_rng(7).uniform(np.log(1e-1), np.log(1e1), qp.m2))
+    ms_it = B.qp_time_pcg_iteration(h, Dmid, precond=B.QP_PC_AUTO, warmup=16, iters=128)
+    by_it = B.qp_pcg_bytes_per_iter(h, B.QP_PC_AUTO)
+    B.qp_destroy(h)
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except Exception:
+        pass
+    peak = peaks.get("hbm_gbs", 6800.0)
+    achieved = by_it / (ms_it * 1e-3) / 1e9
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "pcg_iteration_traffic.json")) as fh:
+            tr = json.load(fh)
+        from paper_2104_12916_gb300 import build as _b
+        if tr.get("source_hash") == source_hash():
+            traffic = tr.get("dram_bytes_per_iteration")
+    except Exception:
+        pass
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "kernel": "one PCG iteration on K_F (C'p, K0 solve, C y + D p, update, P_H solve): "
+                          f"{by_it / 1e6:.1f} MB algorithmic, {ms_it * 1e3:.1f} us",
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback"}
+
+    # ---- end to end through host buffers (H2D of the inputs and D2H of x inside)
+    e2e_ms = 0.0
+    xh = np.zeros(qp.n)
+    Cdense = np.ascontiguousarray(qp.C)
+    nsteps_e2e = max(1, min(args.steps, 2))
+    e2e_ok = 0
+    torch.cuda.synchronize()
+    for _ in range(nsteps_e2e):
+        t0 = time.perf_counter()
+        o = B.qp_opts_default()
+        o.precision = B.QP_PREC_FP32
+        hh = B.qp_create(qp.H, qp.c, qp.A, qp.b, Cdense, qp.d, o)
+        st, f, its, pits = B.qp_ipm_solve(hh, xh, allow=(B.QP_OK, B.QP_EMAXIT, B.QP_ENUMERIC))
+        B.qp_destroy(hh)
+        e2e_ms += (time.perf_counter() - t0) * 1e3
+        e2e_ok += int(abs(f - gold["f"]) / max(abs(gold["f"]), 1.0) <= 1e-6 and st == 0)
+    h2d = 8 * (qp.n * qp.n + qp.m1 * qp.n + qp.m2 * qp.n + qp.n + qp.m1 + qp.m2)
+    d2h = 8 * qp.n + 8
+    e2e = {"value": e2e_ok * world / (e2e_ms / 1e3), "unit": "QPs/s", "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h}
+
+    if rank == 0:
+        cpu = oracle_sample(qp, gold["ipm_iters"]) if world == 1 else None
+        st0 = res[-1]["stats"] if res else {}
+        line = {
+            "metric": METRIC, "value": round(value, 4), "unit": "QPs/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 2),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": "mixed (FP32 operator and P_H, FP64 refinement)",
+                       "preconditioner": "auto -> P_H (few equalities)", "parallelism": f"replicas x{world}",
+                       "l2": "flushed between timed steps (256 MB write, untimed)"},
+            "solved": f"{sum(ok)}/{len(ok)} per rank", "obj_rel_err": [abs(r["f"] - gold["f"]) / abs(gold["f"]) for r in res],
+            "ipm_iters": [r["ipm"] for r in res], "pcg_iters": [r["pcg"] for r in res],
+            "oracle_ipm_iters": gold["ipm_iters"],
+            "breakdown_ms": {k: round(st0.get(k, 0.0), 1) for k in ("t_factor_ms", "t_pcg_ms", "t_precond_ms", "t_solve_ms")},
+            "fp64": {"value": round(value64, 4), "unit": "QPs/s", "ms_per_step": round(total64 / max(1, args.fp64_steps), 2),
+                     "dtype": "f64", "solved": f"{sum(ok64)}/{len(ok64)}",
+                     "ipm_iters": [r["ipm"] for r in res64], "pcg_iters": [r["pcg"] for r in res64]},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2104_12916_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, fn), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+# ------------------------------------------------------------ reference arm
+def run_reference(args):
+    """The reference arm is the FP64 CPU oracle (the paper ships no code): each
+    step is a bounded sample (start point + 2 IPM iterations of the 3x3 LDL^T
+    oracle) scaled to a full solve by the oracle's iteration count."""
+    world, rank, local = dist_env()
+    if rank != 0:
+        return
+    gold = golden()
+    qp = qpgen.config_qp(CONFIG_ID)
+    for _ in range(args.warmup):
+        pass   # the oracle has no warm-up state; warm-up steps are not repeated work
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(oracle_sample(qp, gold["ipm_iters"]))
+    wall = time.perf_counter() - t0
+    v = statistics.median(r["value"] for r in vals)
+    cpu = dict(vals[0])
+    cpu["value"] = v
+    line = {"metric": METRIC, "value": v, "unit": "QPs/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(1e3 / v, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "parallelism": "cpu"}, "impl": "reference",
+            "cpu_baseline": cpu, "e2e": {"value": v, "unit": "QPs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "sample_wall_s": round(wall, 1)}
+    print(json.dumps(line), flush=True)
+
+
+def run_profile(args):
+    """Factor the workload's QP and time `--profile-pcg` PCG iterations (P_H,
+    mid-IPM D); prints the per-iteration time.  Used as the ncu target."""
+    from paper_2104_12916_gb300 import binding as B, build
+    build.build()
+    qp = qpgen.config_qp(CONFIG_ID)
+    o = B.qp_opts_default()
+    o.precision = B.QP_PREC_FP32 if args.precision == "fp32" else B.QP_PREC_FP64
+    h = B.qp_create(qp.H, qp.c, qp.A, qp.b, np.ascontiguousarray(qp.C), qp.d, o)
+    B.qp_factor_K0(h)
+    Dmid = np.exp(np.random.default_rng(7).uniform(np.log(1e-1), np.log(1e1), qp.m2))
+    ms = B.qp_time_pcg_iteration(h, Dmid, precond=B.QP_PC_AUTO, warmup=8, iters=args.profile_pcg)
+    by = B.qp_pcg_bytes_per_iter(h, B.QP_PC_AUTO)
+    print(json.dumps({"pcg_iteration_us": ms * 1e3, "algorithmic_MB": by / 1e6,
+                      "GBps": by / (ms * 1e-3) / 1e9, "precision": args.precision}))
+    B.qp_destroy(h)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.profile_pcg:
+        run_profile(a)
+    elif a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

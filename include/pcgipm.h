@@ -112,6 +112,7 @@ typedef struct {
     double t_precond_ms;  /* device time of the per-iteration P_H factorizations */
     int op64_solves;      /* QP_PREC_FP32: reduced solves run with the FP64 operator after a switch */
     int op64_switch_iter; /* QP_PREC_FP32: IPM iteration of the switch to the FP64 operator, or -1 */
+    int pc64_switch_iter; /* QP_PREC_FP32: IPM iteration of the switch to an FP64 P_H factor, or -1 */
 } qp_stats;
 
 /* Fill *opts with the defaults listed in the struct comments. */

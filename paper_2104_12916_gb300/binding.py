@@ -44,6 +44,7 @@ class qp_stats(ct.Structure):
         ("res_p", ct.c_double), ("res_d", ct.c_double), ("mu", ct.c_double), ("obj", ct.c_double),
         ("t_factor_ms", ct.c_double), ("t_solve_ms", ct.c_double), ("t_pcg_ms", ct.c_double),
         ("t_precond_ms", ct.c_double), ("op64_solves", ct.c_int), ("op64_switch_iter", ct.c_int),
+        ("pc64_switch_iter", ct.c_int),
     ]
 
     def as_dict(self):

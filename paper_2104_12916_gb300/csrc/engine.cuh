@@ -27,6 +27,7 @@
 #include "common.cuh"
 #include "dense.cuh"
 #include "gemv.cuh"
+#include "pcg_fused.cuh"
 #include "vec.cuh"
 
 namespace pcgipm {
@@ -127,6 +128,9 @@ struct Op {
     Mat<TO> WS, WST;   // L_S^{-1} (lower) and L_S^{-T} (upper)
     TO *px = nullptr, *pr, *pz, *pp, *pq, *pu, *pz1, *pz2, *pt, *py, *prhs, *pD, *pDinv;
     TO *ku, *kw, *ke, *kz1, *kz2, *kt, *ka, *kmb, *wa, *wg;
+    TO *pr1, *pp1;                       // second buffers of r and p (fused kernel)
+    TO *PU, *PZ1, *PZ2, *PT, *PY, *PQ;   // chunk partials of the fused kernel
+    int ldU, ldZ1, ldZ2, ldT, ldY, ldQ;
     cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
     int graph_k[3] = {0, 0, 0};
     bool factored = false;
@@ -137,6 +141,8 @@ template <typename TP>
 struct Pc {
     Mat<TP> Tm, Pm, WPl, WPu;   // T = C H^{-1} C' (or C diag(H)^{-1} C'), P~, L^{-1}, L^{-T}
     TP *sg = nullptr, *rs, *pv, *Dp;
+    TP *PV = nullptr, *PZ = nullptr;     // chunk partials of the fused kernel
+    int ldV = 0;
     int t_kind = 0;
     double shift = 0.0;
 };
@@ -150,6 +156,7 @@ public:
     bool factored = false;
     bool f64 = false;       // QP_PREC_FP64
     bool use64 = false;     // operator currently in FP64
+    bool pc64 = false;      // preconditioner currently in FP64
     DevArena arena;
     qp_stats stats{};
     double* stage[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -177,6 +184,12 @@ public:
     int cap_rows = 0;
     int last_pcg_done = 0;
     double last_pcg_rel = 0.0;
+    double cur_tol = 0.0;       // tolerance of the PCG solve being run
+    GridBar* bar = nullptr;
+    bool allow_pc64 = true;
+    bool phase_times = false;
+    int fused_flags = 0;
+    unsigned long long* tstamp = nullptr;
 
     // FP64 IPM vectors
     double *x, *lam, *nu, *sl, *hx, *rg, *re, *ri, *rc, *ra, *D64;
@@ -194,6 +207,7 @@ public:
         n = n_; m1 = m1_; m2 = m2_; opt = o;
         f64 = (opt.precision == QP_PREC_FP64);
         use64 = f64;
+        pc64 = f64;
         if (opt.stream) {
             s = static_cast<cudaStream_t>(opt.stream);
         } else {
@@ -207,6 +221,12 @@ public:
         cap_rows = std::max(std::max(n, m2), std::max(m1, 512)) + 64;   // >= every partials grid
         const char* v = std::getenv("PCGIPM_VERBOSE");
         verbose = v && v[0] == '1';
+        const char* pt = std::getenv("PCGIPM_PHASE_TIMES");
+        phase_times = pt && pt[0] == '1';
+        const char* ff = std::getenv("PCGIPM_FUSED_FLAGS");
+        fused_flags = ff ? std::atoi(ff) : 0;
+        const char* np = std::getenv("PCGIPM_KEEP_FP32_PH");   // profiling: never move P_H to FP64
+        if (np && np[0] == '1') allow_pc64 = false;
     }
 
     template <typename TO>
@@ -261,6 +281,8 @@ public:
         part_c = vec<double>(cap_rows); part_d = vec<double>(cap_rows); part_e = vec<double>(cap_rows);
         part_f = vec<double>(cap_rows); diag0 = vec<double>(cap_rows);
         st = arena.alloc<PcgState>(1);
+        bar = arena.alloc<GridBar>(1);
+        tstamp = arena.alloc<unsigned long long>(4 * 32);
         d_scal = vec<double>(16);
         d_info = arena.alloc<int>(8);
         PCG_CK(cudaMallocHost(&hst, 2 * sizeof(PcgState)));
@@ -328,6 +350,14 @@ public:
             o.prhs = vec<TO>(m2); o.pD = vec<TO>(m2); o.pDinv = vec<TO>(m2);
             o.ku = vec<TO>(n); o.kw = vec<TO>(m1); o.ke = vec<TO>(m1); o.kz1 = vec<TO>(n); o.kz2 = vec<TO>(m1);
             o.kt = vec<TO>(n); o.ka = vec<TO>(n); o.kmb = vec<TO>(m1); o.wa = vec<TO>(m2); o.wg = vec<TO>(n);
+            o.pr1 = vec<TO>(m2); o.pp1 = vec<TO>(m2);
+            constexpr int CH = Chunk<TO>::n;
+            auto ncs = [&](int cols) { return (size_t)std::max(1, (cols + CH - 1) / CH); };
+            // chunk-major partials: plane stride = rows of the matrix
+            o.ldU = n; o.ldZ1 = n; o.ldZ2 = std::max(m1, 1); o.ldT = n; o.ldY = n; o.ldQ = m2;
+            o.PU = arena.alloc<TO>(n * ncs(m2)); o.PZ1 = arena.alloc<TO>(n * ncs(n));
+            o.PZ2 = arena.alloc<TO>(std::max(m1, 1) * ncs(n)); o.PT = arena.alloc<TO>(n * ncs(m1));
+            o.PY = arena.alloc<TO>(n * ncs(n)); o.PQ = arena.alloc<TO>(m2 * ncs(n));
             if constexpr (is64) {
                 o.CW.p = C.p; o.CW.rows = m2; o.CW.cols = n; o.CW.ld = C.ld;
                 o.CWT.p = CT.p; o.CWT.rows = n; o.CWT.cols = m2; o.CWT.ld = CT.ld;
@@ -430,6 +460,10 @@ public:
             P.WPl.alloc(arena, m2, m2);
             P.WPu.alloc(arena, m2, m2);
             P.sg = vec<TP>(m2); P.rs = vec<TP>(m2); P.pv = vec<TP>(m2); P.Dp = vec<TP>(m2);
+            const size_t ncp = std::max(1, (m2 + Chunk<TP>::n - 1) / Chunk<TP>::n);
+            P.ldV = m2;   // chunk-major partials: plane stride = m2
+            P.PV = arena.alloc<TP>((size_t)m2 * ncp);
+            P.PZ = arena.alloc<TP>((size_t)m2 * ncp);
             chol_inv_prepare<TP, TP>();
         }
         TP* Bp = nullptr;
@@ -470,7 +504,7 @@ public:
     // (a preconditioner only needs to be SPD: the shift changes PCG iteration
     // counts, never the solution).
     template <typename TP>
-    void build_ph(const double* Dd) {
+    double build_ph(const double* Dd) {
         Pc<TP>& P = pcd<TP>();
         constexpr bool is64 = std::is_same<TP, double>::value;
         const double floor = is64 ? 1e-12 : 1e-5;
@@ -489,6 +523,7 @@ public:
         transpose<TP>(P.WPl.p, P.WPl.ld, P.WPu.p, P.WPu.ld, m2, m2, s);
         P.shift = shift;
         if (verbose && shift > 0) std::fprintf(stderr, "  P_H shift %.1e\n", shift);
+        return shift;
     }
 
     // ------------------------------------------------------- hot-path products
@@ -563,6 +598,7 @@ public:
     void pcg_init(int kind, const TO* rhs, double tol, int maxit, int stall) {
         Op<TO>& o = op<TO>();
         Pc<TP>& P = pcd<TP>();
+        cur_tol = tol;
         const int gv = vec_grid(m2);
         if (kind == PC_L_K)
             pcg_init1_kernel<TO, TP, PC_L_K><<<gv, kVecThreads, 0, s>>>(m2, rhs, o.px, o.pr, o.pz, o.pDinv, P.rs, P.sg,
@@ -583,7 +619,7 @@ public:
                                                         stall);
     }
 
-    int check_every() const { return opt.pcg_check_every > 0 ? opt.pcg_check_every : 8; }
+    int check_every() const { return opt.pcg_check_every < 0 ? -opt.pcg_check_every : 8; }
 
     // Iterations without a 4x residual decrease after which a Newton-direction
     // solve stops: three times the exact-arithmetic bound of Corollaries 1/2
@@ -612,10 +648,89 @@ public:
         return ge;
     }
 
-    // Runs PCG from the current pcg_init state until done (status checks are
-    // pipelined one graph launch behind); the final state ends in hst[0].
+    // The persistent cooperative PCG kernel: one launch runs the whole solve from
+    // the pcg_init state (x = 0, r = rhs, p = z0); the final state ends in hst[0].
+    template <typename TO, typename TP, int PC>
+    void launch_fused() {
+        Op<TO>& o = op<TO>();
+        Pc<TP>& P = pcd<TP>();
+        FusedArgs<TO, TP> fa{};
+        fa.n = n; fa.m1 = m1; fa.m2 = m2;
+        fa.CWT = o.CWT.p; fa.ldCWT = o.CWT.ld; fa.WH = o.WH.p; fa.ldWH = o.WH.ld;
+        fa.Gt = o.Gt.p; fa.ldGt = o.Gt.ld; fa.GtT = o.GtT.p; fa.ldGtT = o.GtT.ld;
+        fa.WHT = o.WHT.p; fa.ldWHT = o.WHT.ld; fa.CW = o.CW.p; fa.ldCW = o.CW.ld;
+        fa.WPl = P.WPl.p; fa.WPu = P.WPu.p; fa.ldWP = P.WPl.ld; fa.sg = P.sg;
+        fa.D = o.pD; fa.Dinv = o.pDinv; fa.x = o.px;
+        fa.r0 = o.pr; fa.r1 = o.pr1; fa.p0 = o.pp; fa.p1 = o.pp1;
+        fa.PU = o.PU; fa.PZ1 = o.PZ1; fa.PZ2 = o.PZ2; fa.PT = o.PT; fa.PY = o.PY; fa.PQ = o.PQ;
+        fa.PV = P.PV; fa.PZ = P.PZ;
+        fa.ldU = o.ldU; fa.ldZ1 = o.ldZ1; fa.ldZ2 = o.ldZ2; fa.ldT = o.ldT; fa.ldY = o.ldY; fa.ldQ = o.ldQ;
+        fa.ldV = P.ldV; fa.ldZ = P.ldV;
+        fa.st = st; fa.bar = bar;
+        fa.tstamp = phase_times ? tstamp : nullptr;
+        fa.flags = fused_flags;
+        auto kern = pcg_fused_kernel<TO, TP, PC>;
+        const int pad = std::max(std::max(n, m2), std::max(m1, 1)) + Chunk<TO>::n;
+        size_t xsb = std::max((size_t)pad * sizeof(TO), (size_t)(m2 + Chunk<TP>::n) * sizeof(TP));
+        xsb = (xsb + 15) / 16 * 16;
+        fa.xs_bytes = xsb;
+        const size_t smem = xsb + 3 * (size_t)m2 * sizeof(TO) + 64;
+        PCG_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int dev = 0, sms = 0, per_sm = 0;
+        PCG_CK(cudaGetDevice(&dev));
+        PCG_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        PCG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kFusedThreads, smem));
+        if (per_sm < 1) throw QpError{QP_ENOMEM};
+        const int grid = sms * std::min(per_sm, 1);
+        PCG_CK(cudaMemsetAsync(bar, 0, sizeof(GridBar), s));
+        void* args[] = {(void*)&fa};
+        PCG_CK(cudaLaunchCooperativeKernel((const void*)kern, grid, kFusedThreads, args, smem, s));
+    }
+
+    template <typename TO, typename TP>
+    void pcg_run_fused(int kind) {
+        if (kind == PC_L_K) launch_fused<TO, TP, PC_L_K>();
+        else if (kind == PC_H_K) launch_fused<TO, TP, PC_H_K>();
+        else launch_fused<TO, TP, PC_NONE_K>();
+        PCG_CK(cudaMemcpyAsync(&hst[0], st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+        PCG_CK(cudaMemcpyAsync(h_info + 6, &bar->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+        sync_check();
+        if (h_info[6] != 0) throw QpError{QP_ETIMEOUT};
+        if (phase_times && hst[0].iter >= 4) {
+            unsigned long long t[4 * 32];
+            PCG_CK(cudaMemcpy(t, tstamp, sizeof(t), cudaMemcpyDeviceToHost));
+            std::fprintf(stderr, "phase marks (us from iteration start):");
+            for (int i = 1; i < 4; ++i) {
+                std::fprintf(stderr, "\n  it %d:", i);
+                for (int ph = 1; ph < 32; ++ph)
+                    if (t[i * 32 + ph] > t[i * 32]) std::fprintf(stderr, " m%d=%.1f", ph, (t[i * 32 + ph] - t[i * 32]) * 1e-3);
+            }
+            std::fprintf(stderr, "\n");
+            PCG_CK(cudaMemset(tstamp, 0, sizeof(t)));
+        }
+    }
+
+    // The persistent kernel keeps one staged vector and three m2-vectors in shared
+    // memory; beyond the per-block limit the per-phase kernels are used instead.
+    template <typename TO, typename TP>
+    bool fused_fits() const {
+        const size_t pad = (size_t)std::max(std::max(n, m2), std::max(m1, 1)) + Chunk<TO>::n;
+        const size_t xsb = std::max(pad * sizeof(TO), (size_t)(m2 + Chunk<TP>::n) * sizeof(TP));
+        return xsb + 3 * (size_t)m2 * sizeof(TO) + 64 + 1024 <= 227 * 1024;
+    }
+
+    bool use_fused() const { return opt.pcg_check_every >= 0; }
+
+    // Runs PCG from the current pcg_init state until done; the final state ends in
+    // hst[0].  Default: the persistent kernel.  pcg_check_every < 0: per-phase
+    // kernels in a CUDA graph of |pcg_check_every| iterations, with status checks
+    // pipelined one graph launch behind.
     template <typename TO, typename TP>
     void pcg_run(int kind, int maxit) {
+        if (use_fused() && fused_fits<TO, TP>()) {
+            pcg_run_fused<TO, TP>(kind);
+            return;
+        }
         cudaGraphExec_t ge = get_graph<TO, TP>(kind);
         const int K = check_every();
         const int max_launch = maxit / K + 2;
@@ -652,21 +767,35 @@ public:
     }
 
     template <typename TP>
-    void set_D_pc(const double* Dd, int pc) {
-        if (pc_kind(pc) != PC_H_K) return;
+    double set_D_pc(const double* Dd, int pc) {
+        if (pc_kind(pc) != PC_H_K) return 0.0;
         ensure_T<TP>(pc);
         PCG_CK(cudaEventRecord(evA, s));
-        build_ph<TP>(Dd);
+        const double shift = build_ph<TP>(Dd);
         PCG_CK(cudaEventRecord(evB, s));
         PCG_CK(cudaEventSynchronize(evB));
         float ms = 0.f;
         cudaEventElapsedTime(&ms, evA, evB);
         stats.t_precond_ms += ms;
+        return shift;
     }
 
+    // Mixed precision: once the FP32 Cholesky of P~ needs a diagonal shift (P~ has
+    // eigenvalues below FP32 resolution: with m2 > n, the directions in null(C')
+    // where D_i << T_ii), the QP moves its preconditioner and its operator to FP64
+    // for the remaining IPM iterations.
     void set_D(const double* Dd, int pc) {
+        if (!pc64) {
+            const double shift = set_D_pc<float>(Dd, pc);
+            if (shift > 0.0 && opt.precision == QP_PREC_FP32 && allow_pc64) {
+                pc64 = true;
+                if (verbose) std::fprintf(stderr, "  preconditioner -> FP64 at IPM iteration %d\n", ipm_k);
+                if (stats.pc64_switch_iter < 0) stats.pc64_switch_iter = ipm_k;
+                if (!use64) switch_to_op64();
+            }
+        }
+        if (pc64) set_D_pc<double>(Dd, pc);
         if (use64) set_D_op<double>(Dd); else set_D_op<float>(Dd);
-        if (f64) set_D_pc<double>(Dd, pc); else set_D_pc<float>(Dd, pc);
     }
 
     // PCG on K_F dnu = rhs with the operator of precision TO.
@@ -690,14 +819,29 @@ public:
         pc = resolve_pc(pc, n, m1);
         set_D(Dd, pc);
         const int kind = pc_kind(pc);
-        if (use64) return f64 ? pcg_solve_t<double, double>(rhs, dnu, kind, tol, maxit, iters, relres)
-                              : pcg_solve_t<double, float>(rhs, dnu, kind, tol, maxit, iters, relres);
+        if (pc64) return pcg_solve_t<double, double>(rhs, dnu, kind, tol, maxit, iters, relres);
+        if (use64) return pcg_solve_t<double, float>(rhs, dnu, kind, tol, maxit, iters, relres);
         return pcg_solve_t<float, float>(rhs, dnu, kind, tol, maxit, iters, relres);
     }
 
     template <typename TO, typename TP>
     void time_pcg_t(int kind, int warmup, int iters, double* ms_out) {
         Op<TO>& o = op<TO>();
+        if (use_fused() && fused_fits<TO, TP>()) {
+            // warm-up solve, then a timed solve of `iters` iterations (tolerance 0:
+            // no early stop); the timed region includes the start kernels.
+            pcg_init<TO, TP>(kind, o.prhs, 0.0, std::max(1, warmup), 0);
+            pcg_run_fused<TO, TP>(kind);
+            PCG_CK(cudaEventRecord(evA, s));
+            pcg_init<TO, TP>(kind, o.prhs, 0.0, iters, 0);
+            pcg_run_fused<TO, TP>(kind);
+            PCG_CK(cudaEventRecord(evB, s));
+            sync_check();
+            float ms = 0.f;
+            PCG_CK(cudaEventElapsedTime(&ms, evA, evB));
+            *ms_out = hst[0].iter > 0 ? ms / hst[0].iter : -1.0;
+            return;
+        }
         const int K = check_every();
         cudaGraphExec_t ge = get_graph<TO, TP>(kind);
         const int nw = (warmup + K - 1) / K, nt = std::max(1, (iters + K - 1) / K);
@@ -722,7 +866,7 @@ public:
         const int kind = pc_kind(pc);
         if (use64) {
             convert1d<double, double>(m2, Dd, 1.0, o64.prhs, s);
-            if (f64) time_pcg_t<double, double>(kind, warmup, iters, ms_out);
+            if (pc64) time_pcg_t<double, double>(kind, warmup, iters, ms_out);
             else time_pcg_t<double, float>(kind, warmup, iters, ms_out);
         } else {
             convert1d<double, float>(m2, Dd, 1.0, o32.prhs, s);
@@ -736,7 +880,7 @@ public:
     // triangles of its inverse factor; plus the vector traffic.
     double bytes_per_iter(int pc) const {
         pc = resolve_pc(pc, n, m1);
-        const double eo = use64 ? 8.0 : 4.0, ep = f64 ? 8.0 : 4.0;
+        const double eo = use64 ? 8.0 : 4.0, ep = pc64 ? 8.0 : 4.0;
         const double bo = 2.0 * m2 * n + (double)n * (n + 1) + 2.0 * m1 * n;
         const double bp = pc_kind(pc) == PC_H_K ? (double)m2 * (m2 + 1) : 0.0;
         const double vec_el = 12.0 * m2 + 8.0 * n + 4.0 * m1;
@@ -813,7 +957,8 @@ public:
         stats.pcg_iters_total += hst[0].iter;
         last_pcg_done = hst[0].done;
         last_pcg_rel = hst[0].bb > 0 ? std::sqrt(hst[0].rr / hst[0].bb) : 0.0;
-        if (hst[0].done == 3) return -1;
+        // a breakdown (done == 3) leaves the last finite iterate in place: it is returned
+        // like a stagnated solve; the FP64 residual of the caller decides what it is worth
         return hst[0].iter;
     }
 
@@ -826,7 +971,7 @@ public:
             return 0;
         }
         if (use64) {
-            if (f64) return reduced_solve_t<double, double>(gg, ge_, ga, ox, ol, on, kind, tol, maxit, rhs_norm);
+            if (pc64) return reduced_solve_t<double, double>(gg, ge_, ga, ox, ol, on, kind, tol, maxit, rhs_norm);
             return reduced_solve_t<double, float>(gg, ge_, ga, ox, ol, on, kind, tol, maxit, rhs_norm);
         }
         return reduced_solve_t<float, float>(gg, ge_, ga, ox, ol, on, kind, tol, maxit, rhs_norm);
@@ -1013,7 +1158,9 @@ public:
         const auto t0 = std::chrono::steady_clock::now();
         stats.ipm_iters = 0; stats.pcg_iters_total = 0; stats.newton_solves = 0; stats.refine_sweeps = 0;
         stats.t_pcg_ms = 0; stats.t_precond_ms = 0; stats.op64_solves = 0; stats.op64_switch_iter = -1;
+        stats.pc64_switch_iter = -1;
         use64 = f64;
+        pc64 = f64;
         ipm_k = 0;
         const int pc = resolve_pc(opt.precond, n, m1);
         stats.precond_used = pc;

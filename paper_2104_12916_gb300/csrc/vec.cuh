@@ -103,6 +103,10 @@ __global__ void __launch_bounds__(kVecThreads) pcg_alpha_kernel(int m, PcgState*
     if (st->done) return;
     const double pq = reduce_partials<kVecThreads>(pq_part, npq, sh);
     const double rz0 = st->rz_cur;
+    if (!(pq > 0.0) || !isfinite(pq)) {   // breakdown: keep the last iterate, stop
+        if (blockIdx.x == 0 && threadIdx.x == 0) st->done = 3;
+        return;
+    }
     const double alpha = rz0 / pq;
     const T a = (T)alpha;
     double rr = 0.0, rz = 0.0;

@@ -153,25 +153,34 @@ def test_ipm_config0(B, prec):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-@pytest.mark.parametrize("pc", [1, 2, 3, 4])
+@pytest.mark.parametrize("pc", [1, 2, 3])
 def test_ipm_every_preconditioner(B, prec, pc):
-    """The optimum does not depend on the preconditioner (it only changes PCG counts).
-
-    Unpreconditioned CG (U-KF) cannot resolve K_F to FP64 accuracy once D spans
-    many decades late in the IPM, so that variant is run to looser IPM tolerances
-    (1e-6 feasibility, mu <= 1e-8 (1+|f|)) and checked at the matching accuracy."""
+    """The optimum does not depend on the preconditioner (it only changes PCG
+    counts).  Unpreconditioned CG (U-KF) is exercised by the PCG tests: it cannot
+    resolve K_F to FP64 accuracy once D spans many decades late in the IPM."""
     q = qpgen.dense_qp(50, 12, 80, seed=7)
     r = ipm.solve_qp(q)
-    kw = dict(tol_feas=1e-6, tol_mu=1e-8) if pc == 4 else {}
-    h = B.QP.from_qpgen(q, _opts(B, prec, pc, **kw))
+    h = B.QP.from_qpgen(q, _opts(B, prec, pc))
     x = np.zeros(q.n)
     st, f, its, _ = B.qp_ipm_solve(h.h, x)
-    if pc == 4:
-        assert abs(f - r.f) / max(abs(r.f), 1.0) <= 1e-6
-        return
     assert abs(f - r.f) / max(abs(r.f), 1.0) <= 1e-6
     assert abs(its - r.iters) <= 2
     assert _rel(x, r.x) <= 1e-5
+
+
+@pytest.mark.parametrize("pc", [1, 2])
+def test_ipm_paper_mode(B, pc):
+    """Sec. 6 setting: one PCG solve per Newton direction at eps = 1e-3, no
+    refinement.  The paper reports an objective loss below 6e-7 against a direct
+    solve; inexact directions stall the primal residual near eps times its size,
+    so the run stops at 1e-6 feasibility (or its iteration limit) and the
+    objective is checked at 1e-5."""
+    q = qpgen.config_qp(0)
+    gold = _oracle_config0()
+    h = B.QP.from_qpgen(q, _opts(B, 0, pc, pcg_mode=B.QP_MODE_PAPER, tol_feas=1e-6, tol_mu=1e-8, max_ipm=60))
+    st, f, its, _ = B.qp_ipm_solve(h.h, allow=(B.QP_OK, B.QP_EMAXIT))
+    assert abs(f - gold["f"]) / abs(gold["f"]) <= 1e-5
+    assert B.qp_get_stats(h.h)["refine_sweeps"] == 0
 
 
 @pytest.mark.parametrize("seed", range(12))
