@@ -205,6 +205,45 @@ int qp_time_pcg_iteration(qp_t qp, const double *D, int precond, int warmup, int
                           double *ms_per_iter, int ptr_kind);
 
 /*
+ * Largest n accepted by qp_kf_apply_static (its intermediate vectors live in a
+ * fixed device array of 4 * QP_STATIC_MAX_N + QP_STATIC_MAX_N doubles, 320 KiB).
+ */
+#define QP_STATIC_MAX_N 8192
+
+/*
+ * q = K_F p without any device allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory themselves
+ * -- code that runs under a memory allocator it does not own (a framework's
+ * caching allocator, a host application that hands over fixed buffers), inside a
+ * region where cudaMalloc would synchronise the device or is not allowed, or on
+ * a device-memory budget fixed in advance -- and so cannot create a qp_t handle.
+ *
+ * It computes the same product as qp_kf_apply in FP64 from a factored K0 the
+ * caller supplies, all as row-major device arrays with leading dimension equal
+ * to their column count:
+ *   C  (m2 x n)  the inequality matrix,
+ *   WH (n x n)   R^{-T}, the inverse of the lower Cholesky factor of H
+ *                (H = R'R; lower triangle, zeros above it),
+ *   Gt (m1 x n)  L_S^{-1} A R^{-1} with L_S L_S' = A H^{-1} A' (NULL if m1 = 0),
+ *   D, p (m2) inputs, q (m2) output.
+ * Chain: u = C'p, z1 = WH u, z2 = -Gt z1, t = z1 + Gt' z2, y = WH' t,
+ * q = D o p + C y.  Requires 1 <= n <= QP_STATIC_MAX_N, 0 <= m1 <= n, m2 >= 1
+ * (QP_EINVAL otherwise).  It calls no cudaMalloc/cudaFree and no allocating
+ * library routine: the intermediate vectors live in one file-scope device array
+ * that every device which loads the library holds until the process exits.
+ * The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress, with the device current); make that first call before
+ * any stream capture.  The work is enqueued on `stream` (a cudaStream_t cast to
+ * void*, NULL = the default stream) and the call returns without waiting.  All
+ * calls on a device share the array: calls that overlap on the GPU (different
+ * streams, or different host threads) race on it and must be serialised by the
+ * caller.  Every intermediate is written before it is read, so nothing left by
+ * an earlier call affects a later one.
+ */
+int qp_kf_apply_static(int n, int m1, int m2, const double *C, const double *WH, const double *Gt,
+                       const double *D, const double *p, double *q, void *stream);
+
+/*
  * Number of this library's kernel launches that have reached the current
  * device since it was loaded (each kernel counts itself once; graph-launched
  * kernels included).  Synchronises the device.  Returns 0 on a CUDA error.

@@ -25,6 +25,7 @@ EXPORTED = [
     "qp_opts_default", "qp_create", "qp_factor_K0", "qp_kf_apply", "qp_k0_solve",
     "qp_pcg_reduced_solve", "qp_ipm_solve", "qp_get_stats", "qp_device_bytes",
     "qp_pcg_bytes_per_iter", "qp_time_pcg_iteration", "qp_kernel_launches", "qp_destroy", "qp_strerror",
+    "qp_kf_apply_static",
 ]
 
 
@@ -84,6 +85,8 @@ def load(path: str | None = None):
     lib.qp_pcg_bytes_per_iter.argtypes = [P, I]
     lib.qp_pcg_bytes_per_iter.restype = D
     lib.qp_time_pcg_iteration.argtypes = [P, P, I, I, I, ct.POINTER(D), I]
+    lib.qp_kf_apply_static.argtypes = [I, I, I, P, P, P, P, P, P, P]
+    lib.qp_kf_apply_static.restype = I
     lib.qp_kernel_launches.argtypes = []
     lib.qp_kernel_launches.restype = ct.c_ulonglong
     lib.qp_destroy.argtypes = [P]
@@ -215,6 +218,20 @@ def qp_time_pcg_iteration(h, D, precond=QP_PC_AUTO, warmup=8, iters=64) -> float
     _check(load().qp_time_pcg_iteration(h, pD, int(precond), int(warmup), int(iters), ct.byref(ms), kh[0]),
            "qp_time_pcg_iteration")
     return ms.value
+
+
+def qp_kf_apply_static(C, WH, Gt, D, p, q, stream=None):
+    """q = K_F p through the no-allocation entry point (all torch CUDA float64
+    tensors; Gt may be None when m1 = 0).  Enqueued on `stream` (a torch stream
+    or None for the default stream); returns the status."""
+    m2, n = int(C.shape[0]), int(C.shape[1])
+    m1 = 0 if Gt is None else int(Gt.shape[0])
+    kh = [None]
+    args = [_ptr(C, kh), _ptr(WH, kh), _ptr(Gt, kh), _ptr(D, kh), _ptr(p, kh), _ptr(q, kh)]
+    if kh[0] != QP_PTR_DEVICE:
+        raise TypeError("qp_kf_apply_static takes device tensors")
+    sp = None if stream is None else stream.cuda_stream
+    return _check(load().qp_kf_apply_static(n, m1, m2, *args, sp), "qp_kf_apply_static")
 
 
 def qp_kernel_launches() -> int:
