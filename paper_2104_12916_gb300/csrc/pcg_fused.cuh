@@ -113,7 +113,7 @@ __device__ __forceinline__ long long chunk_items(int rows, int cols, int CH) {
 template <int TRI>
 __device__ __forceinline__ void item_at(long long it, int rows, int nc, int CH, int& c, long long& base,
                                         int& row) {
-    if (TRI == TRI_NONE) {
+    if constexpr (TRI == TRI_NONE) {
         c = (int)(it / rows);
         row = (int)(it - (long long)c * rows);
         return;
