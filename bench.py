@@ -212,6 +212,7 @@ def run_ours(args):
 
     # ---- roofline of the dominant kernel chain: one PCG iteration (a6-a10)
     o = opts(B.QP_PREC_FP32)
+    o.mixed_fallback = 0          # the FP32 hot path itself (the mixed solve's first phase)
     h = B.qp_create(Hd, cd, Ad, bd, Cd, dd, o)
     B.qp_factor_K0(h)
     # an early-IPM D (s, nu of order one): the FP32 P_H factor applies, so this times
@@ -292,10 +293,12 @@ def run_ours(args):
 
 
 def source_hash():
+    """Hash of the sources of the persistent PCG kernel (the kernel whose DRAM
+    traffic profiles/pcg_iteration_traffic.json records)."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2104_12916_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
+    for fn in ("common.cuh", "vec.cuh", "pcg_fused.cuh"):
         with open(os.path.join(csrc, fn), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -338,6 +341,7 @@ def run_profile(args):
     qp = qpgen.config_qp(CONFIG_ID)
     o = B.qp_opts_default()
     o.precision = B.QP_PREC_FP32 if args.precision == "fp32" else B.QP_PREC_FP64
+    o.mixed_fallback = 0          # time the FP32 kernels themselves
     h = B.qp_create(qp.H, qp.c, qp.A, qp.b, np.ascontiguousarray(qp.C), qp.d, o)
     B.qp_factor_K0(h)
     Dmid = np.exp(np.random.default_rng(7).uniform(np.log(1e-1), np.log(1e1), qp.m2))

@@ -94,7 +94,10 @@ typedef struct {
     double refine_tol;    /* stop refining when |rho|_2 <= refine_tol |rhs|_2 (default 1e-11) */
     double tol_feas;      /* scaled primal/dual infeasibility tolerance (default 1e-10) */
     double tol_mu;        /* stop when mu <= tol_mu (1 + |f|) (default 1e-11) */
-    int pcg_check_every;  /* PCG iterations per convergence check (default 8) */
+    int pcg_check_every;  /* >= 0: PCG runs as one persistent kernel per solve (default 8, unused);
+                             < 0: per-phase kernels in CUDA graphs of |value| iterations */
+    int mixed_fallback;   /* QP_PREC_FP32 only: 1 (default) lets a QP move its operator and P_H to
+                             FP64 when FP32 stops sufficing; 0 keeps FP32 (shifting P_H as needed) */
     void *stream;         /* cudaStream_t, or NULL for a library-created stream */
 } qp_opts;
 

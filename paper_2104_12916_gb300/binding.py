@@ -34,7 +34,8 @@ class qp_opts(ct.Structure):
         ("precision", ct.c_int), ("precond", ct.c_int), ("pcg_mode", ct.c_int),
         ("max_ipm", ct.c_int), ("max_pcg", ct.c_int), ("refine_max", ct.c_int),
         ("pcg_tol", ct.c_double), ("refine_tol", ct.c_double), ("tol_feas", ct.c_double),
-        ("tol_mu", ct.c_double), ("pcg_check_every", ct.c_int), ("stream", ct.c_void_p),
+        ("tol_mu", ct.c_double), ("pcg_check_every", ct.c_int), ("mixed_fallback", ct.c_int),
+        ("stream", ct.c_void_p),
     ]
 
 

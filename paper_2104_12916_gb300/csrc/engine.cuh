@@ -225,8 +225,7 @@ public:
         phase_times = pt && pt[0] == '1';
         const char* ff = std::getenv("PCGIPM_FUSED_FLAGS");
         fused_flags = ff ? std::atoi(ff) : 0;
-        const char* np = std::getenv("PCGIPM_KEEP_FP32_PH");   // profiling: never move P_H to FP64
-        if (np && np[0] == '1') allow_pc64 = false;
+        allow_pc64 = opt.mixed_fallback != 0;
     }
 
     template <typename TO>
@@ -1040,7 +1039,7 @@ public:
         int budget = opt.refine_max;
         for (int sweep = 0; sweep < budget && prev > rtol2; ++sweep) {
             const double contraction = std::sqrt(prev / last);
-            if (!use64 && sweep > 0 && contraction > 0.25) {
+            if (!use64 && allow_pc64 && sweep > 0 && contraction > 0.25) {
                 switch_to_op64();
                 budget = sweep + opt.refine_max;   // fresh sweeps with the FP64 operator
             }
@@ -1061,7 +1060,7 @@ public:
                 axpby<double, double>(n, -1.0, tx, 1.0, ox, s);
                 if (m1) axpby<double, double>(m1, -1.0, tl, 1.0, ol, s);
                 axpby<double, double>(m2, -1.0, tn, 1.0, on, s);
-                if (use64) break;
+                if (use64 || !allow_pc64) break;
                 kkt3_residual(ox, ol, on);     // restore rho for the next correction
                 switch_to_op64();
                 budget = sweep + 1 + opt.refine_max;

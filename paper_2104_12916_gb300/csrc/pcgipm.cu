@@ -70,6 +70,7 @@ void qp_opts_default(qp_opts* o) {
     o->tol_feas = 1e-10;
     o->tol_mu = 1e-11;
     o->pcg_check_every = 8;
+    o->mixed_fallback = 1;
     o->stream = nullptr;
 }
 
