@@ -185,6 +185,32 @@ int qp_pcg_reduced_solve(qp_t qp, const double *D, const double *rhs, double *dn
 int qp_ipm_solve(qp_t qp, double *x, double *lam, double *nu, double *s,
                  double *obj, int *ipm_iters, long long *pcg_iters_total, int ptr_kind);
 
+/* Per-QP outcome of qp_batch_solve. */
+typedef struct {
+    int status;             /* qp_ipm_solve status of this QP */
+    int ipm_iters;
+    long long pcg_iters;
+    double obj, res_p, res_d, mu;
+    double solve_ms;        /* wall time of this QP's factor + solve */
+} qp_result;
+
+/*
+ * Solve `count` independent QPs (handles from qp_create, possibly of different
+ * sizes) concurrently on the current GPU: up to `max_concurrent` host workers
+ * (0 = 16) each take the next unsolved handle and run qp_factor_K0 and
+ * qp_ipm_solve on that handle's own stream; the persistent PCG kernel of a small
+ * QP uses a grid sized to its per-iteration bytes, so several QPs' kernels share
+ * the GPU.  results[i] receives QP i's outcome; solutions stay in the handles
+ * (qp_get_solution).  Each handle must have been created with opts.stream NULL
+ * (its own stream).  Returns QP_OK when every QP converged, else the first
+ * non-OK status (every QP is attempted).  Batched workloads: the 512 dense QPs of
+ * uneven size (n in [64, 512]) the method is measured on.
+ */
+int qp_batch_solve(qp_t *qps, int count, int max_concurrent, qp_result *results);
+
+/* Copy the last qp_ipm_solve iterate of `qp` (x: n, lam: m1, nu: m2, s: m2; any may be NULL). */
+int qp_get_solution(qp_t qp, double *x, double *lam, double *nu, double *s, int ptr_kind);
+
 /* Copy the handle's counters and timings into *st. */
 int qp_get_stats(qp_t qp, qp_stats *st);
 

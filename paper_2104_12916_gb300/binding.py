@@ -25,7 +25,7 @@ EXPORTED = [
     "qp_opts_default", "qp_create", "qp_factor_K0", "qp_kf_apply", "qp_k0_solve",
     "qp_pcg_reduced_solve", "qp_ipm_solve", "qp_get_stats", "qp_device_bytes",
     "qp_pcg_bytes_per_iter", "qp_time_pcg_iteration", "qp_kernel_launches", "qp_destroy", "qp_strerror",
-    "qp_kf_apply_static",
+    "qp_kf_apply_static", "qp_batch_solve", "qp_get_solution",
 ]
 
 
@@ -37,6 +37,17 @@ class qp_opts(ct.Structure):
         ("tol_mu", ct.c_double), ("pcg_check_every", ct.c_int), ("mixed_fallback", ct.c_int),
         ("stream", ct.c_void_p),
     ]
+
+
+class qp_result(ct.Structure):
+    _fields_ = [
+        ("status", ct.c_int), ("ipm_iters", ct.c_int), ("pcg_iters", ct.c_longlong),
+        ("obj", ct.c_double), ("res_p", ct.c_double), ("res_d", ct.c_double), ("mu", ct.c_double),
+        ("solve_ms", ct.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class qp_stats(ct.Structure):
@@ -86,6 +97,10 @@ def load(path: str | None = None):
     lib.qp_pcg_bytes_per_iter.argtypes = [P, I]
     lib.qp_pcg_bytes_per_iter.restype = D
     lib.qp_time_pcg_iteration.argtypes = [P, P, I, I, I, ct.POINTER(D), I]
+    lib.qp_batch_solve.argtypes = [ct.POINTER(P), I, I, ct.POINTER(qp_result)]
+    lib.qp_batch_solve.restype = I
+    lib.qp_get_solution.argtypes = [P, P, P, P, P, I]
+    lib.qp_get_solution.restype = I
     lib.qp_kf_apply_static.argtypes = [I, I, I, P, P, P, P, P, P, P]
     lib.qp_kf_apply_static.restype = I
     lib.qp_kernel_launches.argtypes = []
@@ -233,6 +248,22 @@ def qp_kf_apply_static(C, WH, Gt, D, p, q, stream=None):
         raise TypeError("qp_kf_apply_static takes device tensors")
     sp = None if stream is None else stream.cuda_stream
     return _check(load().qp_kf_apply_static(n, m1, m2, *args, sp), "qp_kf_apply_static")
+
+
+def qp_batch_solve(handles, max_concurrent=0):
+    """Solve many handles concurrently; returns (status, [result dicts])."""
+    n = len(handles)
+    arr = (ct.c_void_p * n)(*[h.value if isinstance(h, ct.c_void_p) else h for h in handles])
+    res = (qp_result * n)()
+    st = load().qp_batch_solve(arr, n, int(max_concurrent), res)
+    return st, [r.as_dict() for r in res]
+
+
+def qp_get_solution(h, x=None, lam=None, nu=None, s=None):
+    kh = [None]
+    args = (_ptr(x, kh), _ptr(lam, kh), _ptr(nu, kh), _ptr(s, kh))
+    return _check(load().qp_get_solution(h, *args, kh[0] if kh[0] is not None else QP_PTR_HOST),
+                  "qp_get_solution")
 
 
 def qp_kernel_launches() -> int:

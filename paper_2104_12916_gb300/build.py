@@ -29,7 +29,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
         t = os.path.getmtime(LIB)
         if all(os.path.getmtime(p) <= t for p in deps):
             return LIB
-    cmd = [nvcc(), "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC", "-shared",
+    cmd = [nvcc(), "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-pthread", "-shared",
            "-I" + os.path.join(ROOT, "include"), "-o", LIB + ".tmp", *SOURCES]
     if verbose:
         print(" ".join(cmd), flush=True)

@@ -292,14 +292,20 @@ __global__ void __launch_bounds__(256) trmm_rowblock_kernel(T* W, long long ldw,
 template <typename X>
 constexpr size_t two_tiles_bytes() { return 2 * sizeof(X) * kNB * (kNB + 1); }
 
+// Sets the (process-wide) shared-memory attributes once per instantiation; the
+// values are fixed, so concurrent callers agree.
 template <typename T, typename CT>
 inline void chol_inv_prepare() {
-    cudaFuncSetAttribute(potrf_diag_kernel<T, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)two_tiles_bytes<CT>());
-    cudaFuncSetAttribute(trsm_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)two_tiles_bytes<T>());
-    cudaFuncSetAttribute(trmm_rowblock_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)two_tiles_bytes<T>());
+    static const bool done = []() {
+        cudaFuncSetAttribute(potrf_diag_kernel<T, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)two_tiles_bytes<CT>());
+        cudaFuncSetAttribute(trsm_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)two_tiles_bytes<T>());
+        cudaFuncSetAttribute(trmm_rowblock_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)two_tiles_bytes<T>());
+        return true;
+    }();
+    (void)done;
 }
 
 template <typename T>

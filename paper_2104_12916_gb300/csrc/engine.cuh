@@ -32,35 +32,43 @@
 
 namespace pcgipm {
 
-struct CudaError { cudaError_t e; };
+struct CudaError {
+    cudaError_t e;
+    int line;
+};
 struct NoMem {};
 struct QpError { int code; };
 
-#define PCG_CK(x)                                             \
-    do {                                                      \
-        cudaError_t _e = (x);                                 \
-        if (_e != cudaSuccess) throw ::pcgipm::CudaError{_e}; \
+#define PCG_CK(x)                                                       \
+    do {                                                                \
+        cudaError_t _e = (x);                                           \
+        if (_e != cudaSuccess) throw ::pcgipm::CudaError{_e, __LINE__}; \
     } while (0)
 
-// Owns every device allocation of one handle (zero-initialised).
+// Owns every device allocation of one handle (zero-initialised on the handle's
+// stream, so that the zeroing is ordered before the handle's own kernels: the
+// legacy default stream does not order against a non-blocking stream).
 class DevArena {
 public:
     ~DevArena() { release(); }
+    cudaStream_t stream = nullptr;
     template <typename T>
     T* alloc(size_t count) {
         void* p = nullptr;
         const size_t bytes = count * sizeof(T) + 256;
-        if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        if (cudaMallocAsync(&p, bytes, stream) != cudaSuccess) {
             cudaGetLastError();
             throw NoMem{};
         }
-        PCG_CK(cudaMemset(p, 0, bytes));
+        PCG_CK(cudaMemsetAsync(p, 0, bytes, stream));
         ptrs_.push_back(p);
         bytes_ += bytes;
         return static_cast<T*>(p);
     }
+    // Stream-ordered frees: no device-wide synchronisation (cudaFree would wait for
+    // every stream, stalling other QPs solved concurrently).
     void release() {
-        for (void* p : ptrs_) cudaFree(p);
+        for (void* p : ptrs_) cudaFreeAsync(p, stream);
         ptrs_.clear();
     }
     size_t bytes() const { return bytes_; }
@@ -214,6 +222,7 @@ public:
             PCG_CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
             own_stream = true;
         }
+        arena.stream = s;
         PCG_CK(cudaEventCreate(&ev0));
         PCG_CK(cudaEventCreate(&ev1));
         PCG_CK(cudaEventCreate(&evA));
@@ -245,6 +254,7 @@ public:
         cudaEventDestroy(evA);
         cudaEventDestroy(evB);
         arena.release();
+        cudaStreamSynchronize(s);
         if (own_stream) cudaStreamDestroy(s);
     }
 
@@ -377,7 +387,7 @@ public:
         TO *Hw = nullptr, *Aw = nullptr, *G = nullptr, *S = nullptr;
         const long long ldn = pad_ld(n), ldm = pad_ld(std::max(m1, 1));
         auto galloc = [&](TO** p, size_t count) {
-            if (cudaMalloc(p, count * sizeof(TO) + 256) != cudaSuccess) { cudaGetLastError(); throw NoMem{}; }
+            if (cudaMallocAsync(p, count * sizeof(TO) + 256, s) != cudaSuccess) { cudaGetLastError(); throw NoMem{}; }
             PCG_CK(cudaMemsetAsync(*p, 0, count * sizeof(TO) + 256, s));
         };
         galloc(&Hw, (size_t)n * ldn);
@@ -418,11 +428,11 @@ public:
             transpose<TO>(o.WS.p, o.WS.ld, o.WST.p, o.WST.ld, m1, m1, s);
         }
         PCG_CK(cudaMemcpyAsync(h_info, d_info, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        cudaFreeAsync(Hw, s);
+        if (Aw) cudaFreeAsync(Aw, s);
+        if (G) cudaFreeAsync(G, s);
+        if (S) cudaFreeAsync(S, s);
         PCG_CK(cudaStreamSynchronize(s));
-        cudaFree(Hw);
-        if (Aw) cudaFree(Aw);
-        if (G) cudaFree(G);
-        if (S) cudaFree(S);
         PCG_CK(cudaGetLastError());
         if (h_info[0] != 0) throw QpError{QP_ENOTCONVEX};
         if (h_info[2] != 0) throw QpError{QP_ESINGULAR};
@@ -467,7 +477,7 @@ public:
         }
         TP* Bp = nullptr;
         const long long ldb = pad_ld(n);
-        if (cudaMalloc(&Bp, (size_t)m2 * ldb * sizeof(TP) + 256) != cudaSuccess) {
+        if (cudaMallocAsync(&Bp, (size_t)m2 * ldb * sizeof(TP) + 256, s) != cudaSuccess) {
             cudaGetLastError();
             throw NoMem{};
         }
@@ -489,8 +499,8 @@ public:
         h.B = Bp; h.sbk = 1; h.sbj = ldb;
         h.C = P.Tm.p; h.ldc = P.Tm.ld; h.alpha = TP(1); h.beta = TP(0); h.lower_out = 1;
         gemm<TP>(h, s);
+        cudaFreeAsync(Bp, s);
         PCG_CK(cudaStreamSynchronize(s));
-        cudaFree(Bp);
         PCG_CK(cudaGetLastError());
         P.t_kind = kind;
     }
@@ -674,13 +684,22 @@ public:
         xsb = (xsb + 15) / 16 * 16;
         fa.xs_bytes = xsb;
         const size_t smem = xsb + 3 * (size_t)m2 * sizeof(TO) + 64;
-        PCG_CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        // The dynamic shared-memory limit is a per-kernel attribute shared by every
+        // thread of the process: raise it once to the device's opt-in maximum (the
+        // launch itself uses only `smem`), never per call.
+        static const cudaError_t attr_ok = [&]() {
+            int d = 0, optin = 0;
+            cudaGetDevice(&d);
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, d);
+            return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - 1024);
+        }();
+        PCG_CK(attr_ok);
         int dev = 0, sms = 0, per_sm = 0;
         PCG_CK(cudaGetDevice(&dev));
         PCG_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         PCG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kFusedThreads, smem));
         if (per_sm < 1) throw QpError{QP_ENOMEM};
-        const int grid = sms * std::min(per_sm, 1);
+        const int grid = fused_grid(sms);
         PCG_CK(cudaMemsetAsync(bar, 0, sizeof(GridBar), s));
         void* args[] = {(void*)&fa};
         PCG_CK(cudaLaunchCooperativeKernel((const void*)kern, grid, kFusedThreads, args, smem, s));
@@ -697,7 +716,8 @@ public:
         if (h_info[6] != 0) throw QpError{QP_ETIMEOUT};
         if (phase_times && hst[0].iter >= 4) {
             unsigned long long t[4 * 32];
-            PCG_CK(cudaMemcpy(t, tstamp, sizeof(t), cudaMemcpyDeviceToHost));
+            PCG_CK(cudaMemcpyAsync(t, tstamp, sizeof(t), cudaMemcpyDeviceToHost, s));
+            PCG_CK(cudaStreamSynchronize(s));
             std::fprintf(stderr, "phase marks (us from iteration start):");
             for (int i = 1; i < 4; ++i) {
                 std::fprintf(stderr, "\n  it %d:", i);
@@ -705,7 +725,7 @@ public:
                     if (t[i * 32 + ph] > t[i * 32]) std::fprintf(stderr, " m%d=%.1f", ph, (t[i * 32 + ph] - t[i * 32]) * 1e-3);
             }
             std::fprintf(stderr, "\n");
-            PCG_CK(cudaMemset(tstamp, 0, sizeof(t)));
+            PCG_CK(cudaMemsetAsync(tstamp, 0, sizeof(t), s));
         }
     }
 
@@ -719,6 +739,15 @@ public:
     }
 
     bool use_fused() const { return opt.pcg_check_every >= 0; }
+
+    // CTAs of the persistent kernel: one per SM for large QPs; for small ones about
+    // one CTA per 512 KB streamed per iteration (at least 8), so that the kernels
+    // of several QPs solved concurrently share the GPU.
+    int fused_grid(int sms) const {
+        const double by = bytes_per_iter(resolve_pc(opt.precond, n, m1));
+        const int want = (int)std::ceil(by / (512.0 * 1024.0));
+        return std::max(std::min(8, sms), std::min(sms, want));
+    }
 
     // Runs PCG from the current pcg_init state until done; the final state ends in
     // hst[0].  Default: the persistent kernel.  pcg_check_every < 0: per-phase
@@ -749,7 +778,8 @@ public:
             PCG_CK(cudaEventSynchronize(cur == 0 ? ev0 : ev1));
             if (hst[cur].done || !second) {
                 PCG_CK(cudaStreamSynchronize(s));
-                PCG_CK(cudaMemcpy(&hst[0], st, sizeof(PcgState), cudaMemcpyDeviceToHost));
+                PCG_CK(cudaMemcpyAsync(&hst[0], st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
+                PCG_CK(cudaStreamSynchronize(s));
                 break;
             }
             cur = 1 - cur;

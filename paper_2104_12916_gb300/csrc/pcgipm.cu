@@ -1,6 +1,11 @@
 // pcgipm.cu -- C ABI of the GB300 preconditioned inexact IPM (declared in include/pcgipm.h).
+#include <atomic>
+#include <cstdlib>
+#include <chrono>
 #include <cstdio>
 #include <memory>
+#include <thread>
+#include <vector>
 
 #include "engine.cuh"
 
@@ -13,7 +18,9 @@ struct qp_s {
 namespace {
 
 int translate(const CudaError& e) {
-    (void)e;
+    const char* v = std::getenv("PCGIPM_VERBOSE");
+    if (v && v[0] == '1')
+        std::fprintf(stderr, "pcgipm: CUDA error %d (%s) at engine.cuh:%d\n", (int)e.e, cudaGetErrorString(e.e), e.line);
     return QP_ECUDA;
 }
 
@@ -163,6 +170,51 @@ int qp_ipm_solve(qp_t qp, double* x, double* lam, double* nu, double* s, double*
         if (ipm_iters) *ipm_iters = e->stats.ipm_iters;
         if (pcg_iters_total) *pcg_iters_total = e->stats.pcg_iters_total;
         return st;
+    });
+}
+
+int qp_batch_solve(qp_t* qps, int count, int max_concurrent, qp_result* results) {
+    if (!qps || count < 0 || !results) return QP_EINVAL;
+    for (int i = 0; i < count; ++i)
+        if (!qps[i] || !qps[i]->eng->own_stream) return QP_EINVAL;
+    if (count == 0) return QP_OK;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return QP_ECUDA;
+    const int workers = std::max(1, std::min(count, max_concurrent > 0 ? max_concurrent : 16));
+    std::atomic<int> next(0);
+    auto work = [&]() {
+        cudaSetDevice(dev);
+        while (true) {
+            const int i = next.fetch_add(1);
+            if (i >= count) break;
+            Engine* e = qps[i]->eng.get();
+            qp_result r{};
+            const auto t0 = std::chrono::steady_clock::now();
+            r.status = guarded([&]() { return e->ipm_solve(); });
+            r.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+            r.ipm_iters = e->stats.ipm_iters;
+            r.pcg_iters = e->stats.pcg_iters_total;
+            r.obj = e->stats.obj;
+            r.res_p = e->stats.res_p;
+            r.res_d = e->stats.res_d;
+            r.mu = e->stats.mu;
+            results[i] = r;
+        }
+    };
+    std::vector<std::thread> pool;
+    for (int w = 1; w < workers; ++w) pool.emplace_back(work);
+    work();
+    for (auto& t : pool) t.join();
+    for (int i = 0; i < count; ++i)
+        if (results[i].status != QP_OK) return results[i].status;
+    return QP_OK;
+}
+
+int qp_get_solution(qp_t qp, double* x, double* lam, double* nu, double* s, int ptr_kind) {
+    if (!qp) return QP_EINVAL;
+    return guarded([&]() {
+        qp->eng->copy_solution(x, lam, nu, s, ptr_kind == QP_PTR_HOST);
+        return QP_OK;
     });
 }
 

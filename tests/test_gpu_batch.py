@@ -1,0 +1,60 @@
+"""qp_batch_solve: many QPs of uneven size solved concurrently.
+
+Checks each result against the FP64 oracle (relative objective 1e-6, IPM
+iterations within 2) and that a QP's solution does not depend on what it is
+batched with: every reduction runs in a fixed order within its own QP and the
+persistent kernel's grid depends only on the QP's size, so the solution alone
+and in the batch must be bit-identical.
+"""
+import numpy as np
+import pytest
+
+import qpgen
+from oracle import ipm
+
+pytestmark = pytest.mark.gpu
+
+
+def _mini_batch(count, seed0=300):
+    """QPs of the batched workload's recipe (m1 in [0.1n, 0.5n], m2 in [n, 3n])
+    at n in [32, 110] so the CPU oracle stays quick."""
+    out = []
+    for i in range(count):
+        rng = np.random.default_rng(seed0 + i)
+        n = int(rng.integers(32, 111))
+        m1 = int(rng.integers(int(np.ceil(0.1 * n)), n // 2 + 1))
+        m2 = int(rng.integers(n, 3 * n + 1))
+        out.append(qpgen.dense_qp(n, m1, m2, seed=seed0 + 1000 + i))
+    return out
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2104_12916_gb300 import binding, build
+    build.build()
+    binding.load()
+    return binding
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_batch_matches_oracle_and_alone(B, prec):
+    qps = _mini_batch(10)
+    o = B.qp_opts_default()
+    o.precision = prec
+    handles = [B.QP.from_qpgen(q, o) for q in qps]
+    st, res = B.qp_batch_solve([h.h for h in handles], max_concurrent=6)
+    assert st == B.QP_OK, res
+    xs_batch = []
+    for q, h, r in zip(qps, handles, res):
+        x = np.zeros(q.n)
+        B.qp_get_solution(h.h, x)
+        xs_batch.append(x)
+        ref = ipm.solve_qp(q, variant="kkt3")
+        assert abs(r["obj"] - ref.f) / max(abs(ref.f), 1.0) <= 1e-6, (q.name, r, ref.f)
+        assert abs(r["ipm_iters"] - ref.iters) <= 2
+    # the same QPs one at a time give bit-identical solutions
+    for q, xb in zip(qps[:4], xs_batch[:4]):
+        h = B.QP.from_qpgen(q, o)
+        x = np.zeros(q.n)
+        B.qp_ipm_solve(h.h, x)
+        assert np.array_equal(x, xb), q.name
