@@ -43,6 +43,13 @@ def parse():
     ap.add_argument("--profile-pcg", type=int, default=0, metavar="ITERS",
                     help="only factor the QP and run ITERS PCG iterations (a short run for ncu)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"], help="precision of --profile-pcg")
+    ap.add_argument("--workload", default="single", choices=["single", "serving"],
+                    help="serving: a Poisson stream of the served workload's QPs through qp_server_*")
+    ap.add_argument("--requests", type=int, default=64, help="serving: number of requests")
+    ap.add_argument("--rate", type=float, default=50.0, help="serving: arrival rate (requests/s)")
+    ap.add_argument("--budget-gb", type=float, default=150.0, help="serving: HBM admission budget")
+    ap.add_argument("--slots", type=int, default=16, help="serving: QPs in flight at most")
+    ap.add_argument("--max-n", type=int, default=4096, help="serving: skip requests with n above this")
     return ap.parse_args()
 
 
@@ -352,9 +359,82 @@ def run_profile(args):
     B.qp_destroy(h)
 
 
+SERVING_WORKLOAD = ("served stream: n log-uniform [64,4096], m_eq = n U(0.05,0.9), m_in = n U(1,3), "
+                    "C CSR 8 nnz/row, Lambda log-uniform [1e-2,1e2], Poisson arrivals")
+
+
+def run_serving(args):
+    """A Poisson stream of the served workload through qp_server_*: requests are
+    submitted at their arrival times (host buffers: the submission copies them,
+    the server moves them to the device when it admits them), results polled as
+    they complete.  value = solved QPs / (last completion - first arrival); a QP
+    counts as solved when it converged to the IPM tolerances (FP64 residuals);
+    the requests with n <= 256 are also checked against the FP64 oracle."""
+    world, rank, local = dist_env()
+    if rank != 0:
+        return
+    from paper_2104_12916_gb300 import binding as B, build
+    build.build()
+    B.load()
+    idx = [i for i in range(10 * args.requests) if qpgen.serving_dims(i)[0] <= args.max_n][:args.requests]
+    qps = [qpgen.serving_qp(i) for i in idx]
+    arrive = qpgen.arrival_times(len(qps), args.rate)
+    o = B.qp_opts_default()
+    srv = B.Server(budget_bytes=int(args.budget_gb * 1e9), max_slots=args.slots, opts=o)
+    l0 = B.qp_kernel_launches()
+    results = {}
+    pending = {}
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        k = 0
+        while k < len(qps) or pending:
+            now = time.perf_counter() - t0
+            while k < len(qps) and arrive[k] <= now:
+                pending[srv.submit(qps[k])] = k
+                k += 1
+            for t in list(pending):
+                r = srv.poll(t)
+                if r is not None:
+                    results[pending.pop(t)] = (r[0], r[1], time.perf_counter() - t0)
+            if k < len(qps):
+                time.sleep(max(0.0, min(0.002, arrive[k] - (time.perf_counter() - t0))))
+            else:
+                time.sleep(0.001)
+        wall = max(v[2] for v in results.values()) - arrive[0]
+    st = srv.stats()
+    srv.close()
+    launches = B.qp_kernel_launches() - l0
+    lat = np.array([results[i][0]["latency_ms"] for i in range(len(qps))])
+    ok = [results[i][0]["status"] == 0 for i in range(len(qps))]
+    # oracle check of the small requests
+    from oracle import ipm
+    errs = []
+    for i, q in enumerate(qps):
+        if q.n <= 256 and ok[i]:
+            ref = ipm.solve_qp(q, variant="kkt3")
+            errs.append(abs(results[i][0]["obj"] - ref.f) / max(abs(ref.f), 1.0))
+    line = {"metric": "QPs solved/s on a served Poisson stream, with p50/p99 latency",
+            "value": round(sum(ok) / wall, 3), "unit": "QPs/s", "n_gpus": 1, "steps": len(qps), "warmup": 0,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": SERVING_WORKLOAD, "rate_per_s": args.rate, "requests": len(qps),
+                       "max_n": args.max_n, "budget_gb": args.budget_gb, "slots": args.slots,
+                       "precision": "mixed (FP32 operator and P_H, FP64 refinement)"},
+            "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 1), "p99": round(float(np.percentile(lat, 99)), 1),
+                           "max": round(float(lat.max()), 1)},
+            "wait_ms_p50": round(float(np.percentile([results[i][0]["wait_ms"] for i in range(len(qps))], 50)), 1),
+            "solved": f"{sum(ok)}/{len(ok)}", "wall_s": round(wall, 2),
+            "oracle_checked": len(errs), "oracle_max_rel_err": max(errs) if errs else None,
+            "n_range": [min(q.n for q in qps), max(q.n for q in qps)],
+            "server": {k2: st[k2] for k2 in ("peak_reserved_bytes", "peak_device_bytes", "failed")},
+            "gpu_launches": int(launches), "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 if __name__ == "__main__":
     a = parse()
-    if a.profile_pcg:
+    if a.workload == "serving" and a.impl == "ours":
+        run_serving(a)
+    elif a.profile_pcg:
         run_profile(a)
     elif a.impl == "reference":
         run_reference(a)

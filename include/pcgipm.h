@@ -67,7 +67,12 @@ enum qp_precision {
 };
 
 enum qp_precond {
-    QP_PC_AUTO = 0,       /* P_L if m1 >= n/2 else P_H (Corollaries 1 and 2: n-m1+1 vs m1+1 iterations) */
+    QP_PC_AUTO = 0,       /* P_L if m1 >= n/2 else P_H (Corollaries 1 and 2: n-m1+1 vs m1+1 iterations);
+                             a QP started on P_L moves to QP_PC_PH_EXACT for its remaining IPM
+                             iterations once a P_L solve ends without converging: the non-unit
+                             eigenvalues of P_L^{-1} K_F are 1 + lambda(X), X >= 0 unbounded as
+                             entries of D go to 0 (Sec. 4.3, Theorem 1), while those of
+                             P_H^{-1} K_F are 1 - lambda(Y) in (0, 1] (Theorem 2) */
     QP_PC_PL = 1,         /* P_L = D, Sec. 4.2 eq. [preconditioner-1] */
     QP_PC_PH_EXACT = 2,   /* P_H = D + C H^{-1} C', Sec. 4.2 eq. [preconditioner-2] */
     QP_PC_PH_DIAG = 3,    /* P_H with diag(H)^{-1}, the variant of the experiments (Sec. 5.2, PH-KF) */
@@ -103,7 +108,7 @@ typedef struct {
 
 typedef struct {
     int status;           /* last status of qp_ipm_solve */
-    int precond_used;     /* resolved enum qp_precond */
+    int precond_used;     /* resolved enum qp_precond at the end of the last solve */
     int ipm_iters;
     long long pcg_iters_total;
     int newton_solves;    /* reduced solves (predictor + corrector + refinement corrections) */
@@ -116,6 +121,7 @@ typedef struct {
     int op64_solves;      /* QP_PREC_FP32: reduced solves run with the FP64 operator after a switch */
     int op64_switch_iter; /* QP_PREC_FP32: IPM iteration of the switch to the FP64 operator, or -1 */
     int pc64_switch_iter; /* QP_PREC_FP32: IPM iteration of the switch to an FP64 P_H factor, or -1 */
+    int pc_switch_iter;   /* QP_PC_AUTO: IPM iteration of the switch from P_L to P_H, or -1 */
 } qp_stats;
 
 /* Fill *opts with the defaults listed in the struct comments. */
@@ -131,6 +137,20 @@ void qp_opts_default(qp_opts *opts);
 int qp_create(qp_t *out, int n, int m1, int m2,
               const double *H, const double *c, const double *A, const double *b,
               const double *C, const double *d, const qp_opts *opts, int ptr_kind);
+
+/*
+ * qp_create with C given in compressed sparse row form: C_rowptr (m2 + 1 ints,
+ * C_rowptr[0] = 0, non-decreasing), C_colidx (C_rowptr[m2] ints in [0, n)),
+ * C_val (C_rowptr[m2] doubles); entries repeated within a row are summed.  The
+ * pattern is checked on the device (QP_EINVAL for a bad pointer array or column
+ * index).  The sparse pattern is the one the serving workload draws (8 entries
+ * per row; the paper assumes sparse data, Sec. 5); C is expanded into the same
+ * dense device layout as qp_create's, so every later call behaves identically.
+ */
+int qp_create_csr(qp_t *out, int n, int m1, int m2,
+                  const double *H, const double *c, const double *A, const double *b,
+                  const int *C_rowptr, const int *C_colidx, const double *C_val,
+                  const double *d, const qp_opts *opts, int ptr_kind);
 
 /*
  * Setup phase (Sec. 4.1: F is factored once per QP, before the IPM iterations).
@@ -192,6 +212,8 @@ typedef struct {
     long long pcg_iters;
     double obj, res_p, res_d, mu;
     double solve_ms;        /* wall time of this QP's factor + solve */
+    double wait_ms;         /* server: submission to admission (0 in qp_batch_solve) */
+    double latency_ms;      /* server: submission to result ready (solve_ms in qp_batch_solve) */
 } qp_result;
 
 /*
@@ -216,6 +238,15 @@ int qp_get_stats(qp_t qp, qp_stats *st);
 
 /* Bytes of device memory the handle holds (after qp_factor_K0: its peak). */
 size_t qp_device_bytes(qp_t qp);
+
+/*
+ * Upper bound on the device memory a handle of these sizes and options can hold
+ * at any time from qp_create to qp_destroy, setup scratch included: the FP64
+ * problem copies, the operator factor (both precisions when QP_PREC_FP32 may
+ * move to FP64), and the P_H matrices when the preconditioner is or may become
+ * P_H (QP_PC_AUTO).  Used for admission by the server below.  opts may be NULL.
+ */
+size_t qp_device_bytes_bound(int n, int m1, int m2, const qp_opts *opts);
 
 /*
  * Per-PCG-iteration algorithmic traffic of the handle's hot path in bytes,
@@ -271,6 +302,76 @@ int qp_time_pcg_iteration(qp_t qp, const double *D, int precond, int warmup, int
  */
 int qp_kf_apply_static(int n, int m1, int m2, const double *C, const double *WH, const double *Gt,
                        const double *D, const double *p, double *q, void *stream);
+
+/*
+ * Serving (continuous batching).  A server owns a device-memory budget and up
+ * to max_slots QPs in flight on the current GPU.  qp_server_submit copies a
+ * QP's host data into the server and returns at once with a ticket; requests
+ * are admitted in submission order as soon as a slot is free and the request's
+ * qp_device_bytes_bound fits in what the budget has left (a request that does
+ * not fit waits, and those behind it wait too, so a large QP is never starved).
+ * An admitted QP is created, factored and solved on its own stream while others
+ * run, its K0 factor and IPM state resident on the device for the whole solve;
+ * the persistent PCG kernels of QPs in flight share the GPU (each grid sized by
+ * its QP's per-iteration bytes).  When a QP finishes, its device memory is
+ * released and the next requests are admitted.  The paper has no serving layer;
+ * each QP is solved exactly as qp_ipm_solve solves it alone, so results do not
+ * depend on what else is in flight.
+ */
+typedef struct qp_server_s *qp_server_t;
+
+/* One QP of a submission: host pointers, layouts as in qp_create / qp_create_csr
+ * (exactly one of C and C_rowptr non-NULL). */
+typedef struct {
+    int n, m1, m2;
+    const double *H, *c, *A, *b;
+    const double *C;
+    const int *C_rowptr, *C_colidx;
+    const double *C_val;
+    const double *d;
+} qp_problem;
+
+/* Aggregate counters of a server. */
+typedef struct {
+    long long submitted, completed, failed;
+    int queued, active;
+    size_t reserved_bytes;       /* sum of the bounds of the QPs in flight */
+    size_t peak_reserved_bytes;
+    size_t peak_device_bytes;    /* largest qp_device_bytes seen for one QP */
+} qp_server_stats;
+
+/*
+ * Start a server: hbm_budget_bytes of device memory for QPs in flight (0 = 90%
+ * of the device's free memory), max_slots QPs in flight (0 = 16); every QP is
+ * solved with *opts (NULL = defaults; opts->stream must be NULL).
+ */
+int qp_server_create(qp_server_t *out, size_t hbm_budget_bytes, int max_slots, const qp_opts *opts);
+
+/*
+ * Queue one QP (its data is copied before the call returns) and return its
+ * ticket.  QP_EINVAL for bad sizes or pointers; QP_ENOMEM when the QP's bound
+ * exceeds the whole budget (it could never be admitted); QP_ESTATE after
+ * qp_server_destroy began.
+ */
+int qp_server_submit(qp_server_t srv, const qp_problem *qp, unsigned long long *ticket);
+
+/*
+ * Non-blocking: QP_EAGAIN while the ticket's QP is queued or running.  Once it
+ * is done, fills *r (r->status is the solve's status) and copies the solution
+ * into any non-NULL host buffer (x: n, lam: m1, nu: m2, s: m2), releases the
+ * ticket and returns QP_OK.  QP_EINVAL for an unknown or released ticket.
+ */
+int qp_server_poll(qp_server_t srv, unsigned long long ticket, qp_result *r,
+                   double *x, double *lam, double *nu, double *s);
+
+/* Block until every submitted QP is done or timeout_ms passes (< 0: no limit);
+ * QP_ETIMEOUT in the second case. */
+int qp_server_drain(qp_server_t srv, double timeout_ms);
+
+int qp_server_get_stats(qp_server_t srv, qp_server_stats *st);
+
+/* Finish the QPs in flight and the queued ones, stop the workers, free the server. */
+void qp_server_destroy(qp_server_t srv);
 
 /*
  * Number of this library's kernel launches that have reached the current

@@ -25,7 +25,9 @@ EXPORTED = [
     "qp_opts_default", "qp_create", "qp_factor_K0", "qp_kf_apply", "qp_k0_solve",
     "qp_pcg_reduced_solve", "qp_ipm_solve", "qp_get_stats", "qp_device_bytes",
     "qp_pcg_bytes_per_iter", "qp_time_pcg_iteration", "qp_kernel_launches", "qp_destroy", "qp_strerror",
-    "qp_kf_apply_static", "qp_batch_solve", "qp_get_solution",
+    "qp_kf_apply_static", "qp_batch_solve", "qp_get_solution", "qp_create_csr", "qp_device_bytes_bound",
+    "qp_server_create", "qp_server_submit", "qp_server_poll", "qp_server_drain", "qp_server_get_stats",
+    "qp_server_destroy",
 ]
 
 
@@ -43,7 +45,27 @@ class qp_result(ct.Structure):
     _fields_ = [
         ("status", ct.c_int), ("ipm_iters", ct.c_int), ("pcg_iters", ct.c_longlong),
         ("obj", ct.c_double), ("res_p", ct.c_double), ("res_d", ct.c_double), ("mu", ct.c_double),
-        ("solve_ms", ct.c_double),
+        ("solve_ms", ct.c_double), ("wait_ms", ct.c_double), ("latency_ms", ct.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class qp_problem(ct.Structure):
+    _fields_ = [
+        ("n", ct.c_int), ("m1", ct.c_int), ("m2", ct.c_int),
+        ("H", ct.c_void_p), ("c", ct.c_void_p), ("A", ct.c_void_p), ("b", ct.c_void_p),
+        ("C", ct.c_void_p), ("C_rowptr", ct.c_void_p), ("C_colidx", ct.c_void_p), ("C_val", ct.c_void_p),
+        ("d", ct.c_void_p),
+    ]
+
+
+class qp_server_stats(ct.Structure):
+    _fields_ = [
+        ("submitted", ct.c_longlong), ("completed", ct.c_longlong), ("failed", ct.c_longlong),
+        ("queued", ct.c_int), ("active", ct.c_int), ("reserved_bytes", ct.c_size_t),
+        ("peak_reserved_bytes", ct.c_size_t), ("peak_device_bytes", ct.c_size_t),
     ]
 
     def as_dict(self):
@@ -58,6 +80,7 @@ class qp_stats(ct.Structure):
         ("t_factor_ms", ct.c_double), ("t_solve_ms", ct.c_double), ("t_pcg_ms", ct.c_double),
         ("t_precond_ms", ct.c_double), ("op64_solves", ct.c_int), ("op64_switch_iter", ct.c_int),
         ("pc64_switch_iter", ct.c_int),
+        ("pc_switch_iter", ct.c_int),
     ]
 
     def as_dict(self):
@@ -86,6 +109,22 @@ def load(path: str | None = None):
     lib.qp_opts_default.argtypes = [ct.POINTER(qp_opts)]
     lib.qp_opts_default.restype = None
     lib.qp_create.argtypes = [ct.POINTER(P), I, I, I, P, P, P, P, P, P, ct.POINTER(qp_opts), I]
+    lib.qp_create_csr.argtypes = [ct.POINTER(P), I, I, I, P, P, P, P, P, P, P, P, ct.POINTER(qp_opts), I]
+    lib.qp_create_csr.restype = I
+    lib.qp_device_bytes_bound.argtypes = [I, I, I, ct.POINTER(qp_opts)]
+    lib.qp_device_bytes_bound.restype = ct.c_size_t
+    lib.qp_server_create.argtypes = [ct.POINTER(P), ct.c_size_t, I, ct.POINTER(qp_opts)]
+    lib.qp_server_create.restype = I
+    lib.qp_server_submit.argtypes = [P, ct.POINTER(qp_problem), ct.POINTER(ct.c_ulonglong)]
+    lib.qp_server_submit.restype = I
+    lib.qp_server_poll.argtypes = [P, ct.c_ulonglong, ct.POINTER(qp_result), P, P, P, P]
+    lib.qp_server_poll.restype = I
+    lib.qp_server_drain.argtypes = [P, D]
+    lib.qp_server_drain.restype = I
+    lib.qp_server_get_stats.argtypes = [P, ct.POINTER(qp_server_stats)]
+    lib.qp_server_get_stats.restype = I
+    lib.qp_server_destroy.argtypes = [P]
+    lib.qp_server_destroy.restype = None
     lib.qp_factor_K0.argtypes = [P]
     lib.qp_kf_apply.argtypes = [P, P, P, P, I]
     lib.qp_k0_solve.argtypes = [P, P, P, P, P, I]
@@ -170,6 +209,26 @@ def qp_create(H, c, A, b, C, d, opts: qp_opts | None = None):
                           _ptr(C, kh), _ptr(d, kh), ct.byref(opts) if opts is not None else None, kh[0])
     _check(st, "qp_create")
     return h
+
+
+def qp_create_csr(H, c, A, b, rowptr, colidx, val, d, opts: qp_opts | None = None):
+    """qp_create with C in CSR form (host int32 rowptr / colidx, float64 val)."""
+    kh = [None]
+    n = int(H.shape[0])
+    m1 = 0 if A is None else int(A.shape[0])
+    m2 = int(d.shape[0])
+    rp = np.ascontiguousarray(rowptr, dtype=np.int32)
+    ci = np.ascontiguousarray(colidx, dtype=np.int32)
+    h = ct.c_void_p()
+    st = load().qp_create_csr(ct.byref(h), n, m1, m2, _ptr(H, kh), _ptr(c, kh), _ptr(A, kh), _ptr(b, kh),
+                              rp.ctypes.data, ci.ctypes.data, _ptr(np.ascontiguousarray(val, dtype=np.float64), kh),
+                              _ptr(d, kh), ct.byref(opts) if opts is not None else None, kh[0])
+    _check(st, "qp_create_csr")
+    return h
+
+
+def qp_device_bytes_bound(n, m1, m2, opts: qp_opts | None = None) -> int:
+    return int(load().qp_device_bytes_bound(int(n), int(m1), int(m2), ct.byref(opts) if opts is not None else None))
 
 
 def qp_factor_K0(h):
@@ -295,6 +354,78 @@ class QP:
     def close(self):
         if self.h:
             qp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """The serving layer: submit QPs (qpgen.QP), poll or drain their results.
+
+    Server(budget_bytes, max_slots, opts); submit(q) -> ticket;
+    poll(ticket) -> None while pending, else (result dict, x); drain(timeout_ms);
+    stats() -> dict; close()."""
+
+    def __init__(self, budget_bytes=0, max_slots=0, opts: qp_opts | None = None):
+        self.h = ct.c_void_p()
+        _check(load().qp_server_create(ct.byref(self.h), int(budget_bytes), int(max_slots),
+                                       ct.byref(opts) if opts is not None else None), "qp_server_create")
+        self._dims = {}
+
+    def submit(self, q) -> int:
+        keep = []
+
+        def p(a, dtype=np.float64):
+            if a is None:
+                return None
+            a = np.ascontiguousarray(a, dtype=dtype)
+            keep.append(a)
+            return a.ctypes.data
+
+        pr = qp_problem()
+        pr.n, pr.m1, pr.m2 = q.n, q.m1, q.m2
+        pr.H, pr.c, pr.d = p(q.H), p(q.c), p(q.d)
+        pr.A = p(q.A) if q.m1 else None
+        pr.b = p(q.b) if q.m1 else None
+        if q.C_csr is not None:
+            rp, ci, val = q.C_csr
+            pr.C_rowptr, pr.C_colidx, pr.C_val = p(rp, np.int32), p(ci, np.int32), p(val)
+            pr.C = None
+        else:
+            pr.C = p(q.C)
+        t = ct.c_ulonglong(0)
+        _check(load().qp_server_submit(self.h, ct.byref(pr), ct.byref(t)), "qp_server_submit")
+        self._dims[t.value] = (q.n, q.m1, q.m2)
+        return t.value
+
+    def poll(self, ticket, want_x=True):
+        n = self._dims.get(ticket, (0, 0, 0))[0]
+        want_x = want_x and n > 0
+        r = qp_result()
+        x = np.zeros(n) if want_x else None
+        st = load().qp_server_poll(self.h, ct.c_ulonglong(ticket), ct.byref(r),
+                                   x.ctypes.data if want_x else None, None, None, None)
+        if st == QP_EAGAIN:
+            return None
+        _check(st, "qp_server_poll")
+        self._dims.pop(ticket, None)
+        return r.as_dict(), x
+
+    def drain(self, timeout_ms=-1.0):
+        return _check(load().qp_server_drain(self.h, float(timeout_ms)), "qp_server_drain")
+
+    def stats(self) -> dict:
+        s = qp_server_stats()
+        _check(load().qp_server_get_stats(self.h, ct.byref(s)), "qp_server_get_stats")
+        return s.as_dict()
+
+    def close(self):
+        if self.h:
+            load().qp_server_destroy(self.h)
             self.h = None
 
     def __del__(self):

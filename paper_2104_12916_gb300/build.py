@@ -11,7 +11,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libpcgipm.so")
-SOURCES = [os.path.join(CSRC, "pcgipm.cu"), os.path.join(CSRC, "kf_static.cu")]
+SOURCES = [os.path.join(CSRC, "pcgipm.cu"), os.path.join(CSRC, "kf_static.cu"), os.path.join(CSRC, "server.cpp")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -133,6 +133,7 @@ struct Op {
     Mat<TO> CW, CWT;   // C and C'
     Mat<TO> WH, WHT;   // R^{-T} = L_H^{-1} (lower) and R^{-1} (upper), H = R'R
     Mat<TO> Gt, GtT;   // L_S^{-1} A R^{-1} and its transpose, L_S L_S' = A H^{-1} A'
+    Mat<TO> Et, EtT;   // Gt R^{-T} = L_S^{-1} A H^{-1} (the (2,1) block of L^{-1}) and its transpose
     Mat<TO> WS, WST;   // L_S^{-1} (lower) and L_S^{-T} (upper)
     TO *px = nullptr, *pr, *pz, *pp, *pq, *pu, *pz1, *pz2, *pt, *py, *prhs, *pD, *pDinv;
     TO *ku, *kw, *ke, *kz1, *kz2, *kt, *ka, *kmb, *wa, *wg;
@@ -195,8 +196,12 @@ public:
     double cur_tol = 0.0;       // tolerance of the PCG solve being run
     GridBar* bar = nullptr;
     bool allow_pc64 = true;
+    int ipm_pc = 0;             // preconditioner of the IPM solve in progress (enum qp_precond)
+    const void* cl_key = nullptr;   // last cluster-launch check: kernel, grid, shared memory, result
+    int cl_grid = 0;
+    size_t cl_smem = 0;
+    bool cl_ok = false;
     bool phase_times = false;
-    int fused_flags = 0;
     unsigned long long* tstamp = nullptr;
 
     // FP64 IPM vectors
@@ -232,8 +237,6 @@ public:
         verbose = v && v[0] == '1';
         const char* pt = std::getenv("PCGIPM_PHASE_TIMES");
         phase_times = pt && pt[0] == '1';
-        const char* ff = std::getenv("PCGIPM_FUSED_FLAGS");
-        fused_flags = ff ? std::atoi(ff) : 0;
         allow_pc64 = opt.mixed_fallback != 0;
     }
 
@@ -261,14 +264,65 @@ public:
     template <typename X>
     X* vec(int len) { return arena.alloc<X>((size_t)pad_ld(len > 0 ? len : 1)); }
 
+    // Upper bound on the device bytes a handle of these sizes holds at any time:
+    // every arena allocation below plus the setup scratch (the factor's working
+    // copies, the C R^{-1} product of T), counted at their padded sizes with the
+    // arena's 256-byte slack, for each precision and preconditioner the options
+    // allow the solve to reach (FP32 may move to FP64; AUTO may move to P_H).
+    static size_t bytes_bound(int n, int m1, int m2, const qp_opts& o) {
+        auto mat = [](int r, int c, size_t es) {
+            return (size_t)std::max(r, 1) * (size_t)pad_ld(std::max(c, 1)) * es + 256;
+        };
+        auto v = [](int len, size_t es) { return (size_t)pad_ld(std::max(len, 1)) * es + 256; };
+        const int cap = std::max(std::max(n, m2), std::max(m1, 512)) + 64;
+        size_t b = 0;
+        // FP64 problem copies, IPM / refinement vectors, partials, staging, scalars
+        b += mat(n, n, 8) + mat(m1, n, 8) + mat(n, m1, 8) + mat(m2, n, 8) + mat(n, m2, 8);
+        b += 64 * v(cap, 8) + 4096;
+        auto op = [&](size_t es, bool copyC) {
+            const int CH = (int)(kSlotBytes / es);
+            auto ncs = [&](int cols) { return (size_t)std::max(1, (cols + CH - 1) / CH); };
+            size_t t = 32 * v(cap, es);
+            t += ((size_t)4 * n + std::max(m1, 1) + m2) * ncs(std::max(n, std::max(m1, m2))) * es + 6 * 256;
+            if (copyC) t += mat(m2, n, es) + mat(n, m2, es);
+            t += 2 * mat(n, n, es);
+            if (m1) t += 2 * mat(m1, m1, es) + 2 * mat(m1, n, es) + 2 * mat(n, m1, es);
+            t += mat(n, n, es) + 2 * mat(m1, n, es) + mat(m1, m1, es);   // factor scratch
+            return t;
+        };
+        auto pc = [&](size_t es) {
+            const int CH = (int)(kSlotBytes / es);
+            const size_t ncp = (size_t)std::max(1, (m2 + CH - 1) / CH);
+            return 4 * mat(m2, m2, es) + 4 * v(m2, es) + 2 * ((size_t)m2 * ncp * es + 256) + mat(m2, n, es);
+        };
+        const bool fp32 = (o.precision == QP_PREC_FP32);
+        const bool ph = o.precond != QP_PC_PL && o.precond != QP_PC_NONE;
+        if (fp32) {
+            b += op(4, true);
+            if (o.mixed_fallback) b += op(8, false);
+            if (ph) b += pc(4) + (o.mixed_fallback ? pc(8) : 0);
+        } else {
+            b += op(8, false);
+            if (ph) b += pc(8);
+        }
+        return b;
+    }
+
     void sync_check() {
         PCG_CK(cudaStreamSynchronize(s));
         PCG_CK(cudaGetLastError());
     }
 
     // ------------------------------------------------------------------ create
+    // C is dense (Ch) or CSR (csr != null; C arrives zeroed from the arena and the
+    // pattern is expanded into it on the device).
+    struct CsrIn {
+        const int* rowptr;
+        const int* colidx;
+        const double* val;
+    };
     void load(const double* Hh, const double* ch, const double* Ah, const double* bh, const double* Ch,
-              const double* dh, int ptr_kind) {
+              const double* dh, int ptr_kind, const CsrIn* csr = nullptr) {
         const cudaMemcpyKind kind = (ptr_kind == QP_PTR_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
         H.alloc(arena, n, n);
         A.alloc(arena, m1, n);
@@ -278,7 +332,39 @@ public:
         c = vec<double>(n); b = vec<double>(m1); d = vec<double>(m2);
         PCG_CK(cudaMemcpy2DAsync(H.p, H.ld * 8, Hh, (size_t)n * 8, (size_t)n * 8, n, kind, s));
         if (m1) PCG_CK(cudaMemcpy2DAsync(A.p, A.ld * 8, Ah, (size_t)n * 8, (size_t)n * 8, m1, kind, s));
-        PCG_CK(cudaMemcpy2DAsync(C.p, C.ld * 8, Ch, (size_t)n * 8, (size_t)n * 8, m2, kind, s));
+        int* csr_bad = nullptr;
+        if (csr) {
+            int last = 0;
+            if (ptr_kind == QP_PTR_HOST) {
+                last = csr->rowptr[m2];
+            } else {
+                PCG_CK(cudaMemcpyAsync(&last, csr->rowptr + m2, sizeof(int), cudaMemcpyDeviceToHost, s));
+                PCG_CK(cudaStreamSynchronize(s));
+            }
+            if (last < 0) throw QpError{QP_EINVAL};
+            const long long nnz = last;
+            csr_bad = arena.alloc<int>(1);
+            const int* rp = csr->rowptr;
+            const int* ci = csr->colidx;
+            const double* cv = csr->val;
+            void* tmp = nullptr;
+            if (ptr_kind == QP_PTR_HOST) {
+                const size_t bytes = (size_t)(m2 + 1) * 4 + (size_t)nnz * 4 + (size_t)nnz * 8 + 64;
+                if (cudaMallocAsync(&tmp, bytes, s) != cudaSuccess) { cudaGetLastError(); throw NoMem{}; }
+                char* t = static_cast<char*>(tmp);
+                double* dv = reinterpret_cast<double*>(t);
+                int* dr = reinterpret_cast<int*>(t + (size_t)nnz * 8);
+                int* dc = dr + (m2 + 1);
+                if (nnz) PCG_CK(cudaMemcpyAsync(dv, cv, (size_t)nnz * 8, kind, s));
+                PCG_CK(cudaMemcpyAsync(dr, rp, (size_t)(m2 + 1) * 4, kind, s));
+                if (nnz) PCG_CK(cudaMemcpyAsync(dc, ci, (size_t)nnz * 4, kind, s));
+                rp = dr; ci = dc; cv = dv;
+            }
+            csr_scatter_kernel<<<(m2 + 255) / 256, 256, 0, s>>>(m2, n, nnz, rp, ci, cv, C.p, C.ld, csr_bad);
+            if (tmp) cudaFreeAsync(tmp, s);
+        } else {
+            PCG_CK(cudaMemcpy2DAsync(C.p, C.ld * 8, Ch, (size_t)n * 8, (size_t)n * 8, m2, kind, s));
+        }
         PCG_CK(cudaMemcpyAsync(c, ch, (size_t)n * 8, kind, s));
         if (m1) PCG_CK(cudaMemcpyAsync(b, bh, (size_t)m1 * 8, kind, s));
         PCG_CK(cudaMemcpyAsync(d, dh, (size_t)m2 * 8, kind, s));
@@ -322,7 +408,10 @@ public:
         reduce_jobs_kernel<<<1, kVecThreads, 0, s>>>(job, d_scal);
         PCG_CK(cudaMemcpyAsync(h_scal, d_scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
         PCG_CK(cudaMemcpyAsync(h_info, d_info, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        if (csr_bad) PCG_CK(cudaMemcpyAsync(h_info + 2, csr_bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+        else h_info[2] = 0;
         sync_check();
+        if (h_info[2] != 0) throw QpError{QP_EINVAL};
         h_norm_inf = h_scal[0]; c_inf = h_scal[1]; b_inf = m1 ? h_scal[2] : 0.0; d_inf = h_scal[3];
         float asym;
         std::memcpy(&asym, &h_info[1], sizeof(float));
@@ -381,6 +470,7 @@ public:
             if (m1) {
                 o.WS.alloc(arena, m1, m1); o.WST.alloc(arena, m1, m1);
                 o.Gt.alloc(arena, m1, n); o.GtT.alloc(arena, n, m1);
+                o.Et.alloc(arena, m1, n); o.EtT.alloc(arena, n, m1);
             }
         }
         // scratch of the factorization (freed at the end)
@@ -426,6 +516,15 @@ public:
             gemm<TO>(k, s);
             transpose<TO>(o.Gt.p, o.Gt.ld, o.GtT.p, o.GtT.ld, m1, n, s);
             transpose<TO>(o.WS.p, o.WS.ld, o.WST.p, o.WST.ld, m1, m1, s);
+            // Et = Gt R^{-T}: with it the forward solve with L maps u to [R^{-T} u; -Et u]
+            // in one product, and the back solve is y = R^{-1} z1 + Et' z2 (z2 = -Et u)
+            GemmArgs<TO> e{};
+            e.M = m1; e.N = n; e.K = n;
+            e.A = o.Gt.p; e.sai = o.Gt.ld; e.sak = 1;
+            e.B = o.WH.p; e.sbk = o.WH.ld; e.sbj = 1; e.b_tri = TRI_LOWER;
+            e.C = o.Et.p; e.ldc = o.Et.ld; e.alpha = TO(1); e.beta = TO(0);
+            gemm<TO>(e, s);
+            transpose<TO>(o.Et.p, o.Et.ld, o.EtT.p, o.EtT.ld, m1, n, s);
         }
         PCG_CK(cudaMemcpyAsync(h_info, d_info, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
         cudaFreeAsync(Hw, s);
@@ -666,7 +765,7 @@ public:
         FusedArgs<TO, TP> fa{};
         fa.n = n; fa.m1 = m1; fa.m2 = m2;
         fa.CWT = o.CWT.p; fa.ldCWT = o.CWT.ld; fa.WH = o.WH.p; fa.ldWH = o.WH.ld;
-        fa.Gt = o.Gt.p; fa.ldGt = o.Gt.ld; fa.GtT = o.GtT.p; fa.ldGtT = o.GtT.ld;
+        fa.Et = o.Et.p; fa.ldEt = o.Et.ld; fa.EtT = o.EtT.p; fa.ldEtT = o.EtT.ld;
         fa.WHT = o.WHT.p; fa.ldWHT = o.WHT.ld; fa.CW = o.CW.p; fa.ldCW = o.CW.ld;
         fa.WPl = P.WPl.p; fa.WPu = P.WPu.p; fa.ldWP = P.WPl.ld; fa.sg = P.sg;
         fa.D = o.pD; fa.Dinv = o.pDinv; fa.x = o.px;
@@ -677,32 +776,67 @@ public:
         fa.ldV = P.ldV; fa.ldZ = P.ldV;
         fa.st = st; fa.bar = bar;
         fa.tstamp = phase_times ? tstamp : nullptr;
-        fa.flags = fused_flags;
         auto kern = pcg_fused_kernel<TO, TP, PC>;
-        const int pad = std::max(std::max(n, m2), std::max(m1, 1)) + Chunk<TO>::n;
-        size_t xsb = std::max((size_t)pad * sizeof(TO), (size_t)(m2 + Chunk<TP>::n) * sizeof(TP));
-        xsb = (xsb + 15) / 16 * 16;
+        const size_t xsb = fused_xs_bytes<TO, TP>();
         fa.xs_bytes = xsb;
-        const size_t smem = xsb + 3 * (size_t)m2 * sizeof(TO) + 64;
-        // The dynamic shared-memory limit is a per-kernel attribute shared by every
-        // thread of the process: raise it once to the device's opt-in maximum (the
-        // launch itself uses only `smem`), never per call.
-        static const cudaError_t attr_ok = [&]() {
-            int d = 0, optin = 0;
-            cudaGetDevice(&d);
-            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, d);
-            return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - 1024);
-        }();
-        PCG_CK(attr_ok);
+        fa.ring_off = fused_ring_offset<TO>(xsb, m2);
         int dev = 0, sms = 0, per_sm = 0;
         PCG_CK(cudaGetDevice(&dev));
         PCG_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        PCG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kFusedThreads, smem));
-        if (per_sm < 1) throw QpError{QP_ENOMEM};
         const int grid = fused_grid(sms);
+        // A QP whose grid covers most of the GPU takes the deepest ring that fits; a
+        // small one (batched with others) a shallow ring, so that the blocks of several
+        // QPs share an SM.
+        fa.slots = fused_slots<TO, TP>();
+        if (2 * grid < sms) fa.slots = std::min(fa.slots, kSmallRingSlots);
+        if (fa.slots < kMinSlots) throw QpError{QP_ENOMEM};
+        const size_t smem = fused_smem_bytes(fa.ring_off, fa.slots);
+        // Kernel attributes are shared by every thread of the process: set them once
+        // (the dynamic shared-memory limit to what fused_slots() sizes the ring for;
+        // the launch itself uses only `smem`), never per call.
+        static const cudaError_t attr_ok = [&]() {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)fused_smem_limit());
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            return e;
+        }();
+        PCG_CK(attr_ok);
+        PCG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kFusedBlock, smem));
+        if (per_sm < 1) throw QpError{QP_ENOMEM};
         PCG_CK(cudaMemsetAsync(bar, 0, sizeof(GridBar), s));
-        void* args[] = {(void*)&fa};
-        PCG_CK(cudaLaunchCooperativeKernel((const void*)kern, grid, kFusedThreads, args, smem, s));
+        // A grid of at most kMaxClusterBlocks blocks is launched as one thread-block
+        // cluster: the hardware schedules the blocks of a cluster together, which is all
+        // the grid barrier needs, and the cluster launches of QPs solved at the same
+        // time run side by side.  Larger grids use a cooperative launch.
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(kFusedBlock);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = grid;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        bool cluster = false;
+        if (grid <= kMaxClusterBlocks) {
+            const void* key = (const void*)kern;
+            if (cl_key != key || cl_grid != grid || cl_smem != smem) {
+                int nclusters = 0;
+                cl_ok = cudaOccupancyMaxActiveClusters(&nclusters, kern, &cfg) == cudaSuccess && nclusters > 0;
+                cudaGetLastError();
+                cl_key = key; cl_grid = grid; cl_smem = smem;
+            }
+            cluster = cl_ok;
+        }
+        if (cluster) {
+            PCG_CK(cudaLaunchKernelEx(&cfg, kern, fa));
+        } else {
+            void* args[] = {(void*)&fa};
+            PCG_CK(cudaLaunchCooperativeKernel((const void*)kern, grid, kFusedBlock, args, smem, s));
+        }
     }
 
     template <typename TO, typename TP>
@@ -729,24 +863,55 @@ public:
         }
     }
 
-    // The persistent kernel keeps one staged vector and three m2-vectors in shared
-    // memory; beyond the per-block limit the per-phase kernels are used instead.
+    // Shared memory of the persistent kernel: one staged vector, three m2-vectors,
+    // and a ring of 4 KB chunk slots as deep as the rest of the block's limit allows
+    // (at most kMaxSlots).  With fewer than kMinSlots slots the per-phase kernels
+    // are used instead.
+    static size_t fused_smem_limit() {
+        static const size_t lim = []() {
+            int d = 0, optin = 0;
+            cudaGetDevice(&d);
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, d);
+            if (optin <= 0) optin = 227 * 1024;
+            return (size_t)optin - 1024;   // static shared memory of the kernel (scalars) below 1 KB
+        }();
+        return lim;
+    }
+    // staged vector: p (m2), u or y (n), z1 and z2 side by side (n + m1), or r for P_H (m2 in TP),
+    // each padded to whole chunks
+    template <typename TO, typename TP>
+    size_t fused_xs_bytes() const {
+        const size_t CO = Chunk<TO>::n, CP = Chunk<TP>::n;
+        auto padto = [](size_t v, size_t c) { return (v + c - 1) / c * c; };
+        const size_t elems = std::max(std::max(padto(n, CO), padto(m2, CO)), padto(n, CO) + padto(std::max(m1, 1), CO));
+        const size_t xsb = std::max(elems * sizeof(TO), padto(m2, CP) * sizeof(TP));
+        return (xsb + 15) / 16 * 16;
+    }
+    template <typename TO, typename TP>
+    int fused_slots() const {
+        const size_t off = fused_ring_offset<TO>(fused_xs_bytes<TO, TP>(), m2);
+        const size_t lim = fused_smem_limit();
+        const size_t per = kSlotBytes + 2 * sizeof(uint64_t) + sizeof(int);
+        if (off + 16 + per > lim) return 0;
+        const int sl = (int)std::min<size_t>(kMaxSlots, (lim - off - 16) / per);
+        return sl / kFusedWarps * kFusedWarps;   // the ring protocol wants a multiple of the consumer warps
+    }
     template <typename TO, typename TP>
     bool fused_fits() const {
-        const size_t pad = (size_t)std::max(std::max(n, m2), std::max(m1, 1)) + Chunk<TO>::n;
-        const size_t xsb = std::max(pad * sizeof(TO), (size_t)(m2 + Chunk<TP>::n) * sizeof(TP));
-        return xsb + 3 * (size_t)m2 * sizeof(TO) + 64 + 1024 <= 227 * 1024;
+        return fused_slots<TO, TP>() >= kMinSlots;
     }
 
     bool use_fused() const { return opt.pcg_check_every >= 0; }
 
-    // CTAs of the persistent kernel: one per SM for large QPs; for small ones about
-    // one CTA per 512 KB streamed per iteration (at least 8), so that the kernels
-    // of several QPs solved concurrently share the GPU.
+    // CTAs of the persistent kernel: about one per 512 KB streamed per iteration,
+    // up to one per SM; a QP of at most 32 such units gets between 8 and
+    // kMaxClusterBlocks (one cluster), so that the kernels of several QPs solved
+    // concurrently share the GPU.
     int fused_grid(int sms) const {
         const double by = bytes_per_iter(resolve_pc(opt.precond, n, m1));
         const int want = (int)std::ceil(by / (512.0 * 1024.0));
-        return std::max(std::min(8, sms), std::min(sms, want));
+        if (want <= 2 * kMaxClusterBlocks) return std::min(sms, std::max(8, std::min(want, kMaxClusterBlocks)));
+        return std::min(sms, want);
     }
 
     // Runs PCG from the current pcg_init state until done; the final state ends in
@@ -1032,6 +1197,19 @@ public:
         return h_scal[0] + (m1 ? h_scal[1] : 0.0) + h_scal[2];
     }
 
+    // QP_PC_AUTO: move a QP from P_L to the exact P_H for the rest of its IPM
+    // iterations.  Late in the IPM the non-unit eigenvalues 1 + lambda(X) of
+    // P_L^{-1} K_F grow without bound as entries of D = V^{-1}S go to zero (Sec. 4.3,
+    // Theorem 1) and PCG stops converging; P_H^{-1} K_F keeps its spectrum in (0, 1]
+    // (Theorem 2).
+    void switch_to_ph() {
+        ipm_pc = QP_PC_PH_EXACT;
+        stats.precond_used = ipm_pc;
+        stats.pc_switch_iter = ipm_k;
+        if (verbose) std::fprintf(stderr, "  preconditioner P_L -> P_H at IPM iteration %d\n", ipm_k);
+        set_D(D64, ipm_pc);
+    }
+
     // Move the operator to FP64 for the rest of the QP (mixed precision mode).
     void switch_to_op64() {
         if (use64) return;
@@ -1048,7 +1226,8 @@ public:
     // corrections are then solved only to half that contraction, and a contraction
     // worse than 1/4 (or a correction that increases the residual) moves the QP to the
     // FP64 operator.
-    int newton_solve(double* ox, double* ol, double* on, int kind) {
+    int newton_solve(double* ox, double* ol, double* on) {
+        const int kind = pc_kind(ipm_pc);
         const bool paper = (opt.pcg_mode == QP_MODE_PAPER);
         const int maxit = opt.max_pcg > 0 ? opt.max_pcg : 4 * m2 + 50;
         auto base_tol = [&]() {
@@ -1061,6 +1240,11 @@ public:
         if (verbose) std::fprintf(stderr, "    solve: |f|=%.3e pcg=%d done=%d rel=%.2e op64=%d\n", std::sqrt(fnorm2),
                                   it, last_pcg_done, last_pcg_rel, (int)use64);
         if (it < 0) return QP_ENUMERIC;
+        if (opt.precond == QP_PC_AUTO && kind == PC_L_K && last_pcg_done >= 2 && last_pcg_rel > base_tol()) {
+            // P_L ran out of iterations, broke down or stagnated: redo with P_H
+            switch_to_ph();
+            return newton_solve(ox, ol, on);
+        }
         if (paper) return QP_OK;
         double prev = kkt3_residual(ox, ol, on);
         const double rtol2 = opt.refine_tol * opt.refine_tol * fnorm2;
@@ -1187,13 +1371,12 @@ public:
         const auto t0 = std::chrono::steady_clock::now();
         stats.ipm_iters = 0; stats.pcg_iters_total = 0; stats.newton_solves = 0; stats.refine_sweeps = 0;
         stats.t_pcg_ms = 0; stats.t_precond_ms = 0; stats.op64_solves = 0; stats.op64_switch_iter = -1;
-        stats.pc64_switch_iter = -1;
+        stats.pc64_switch_iter = -1; stats.pc_switch_iter = -1;
         use64 = f64;
         pc64 = f64;
         ipm_k = 0;
-        const int pc = resolve_pc(opt.precond, n, m1);
-        stats.precond_used = pc;
-        const int kind = pc_kind(pc);
+        ipm_pc = resolve_pc(opt.precond, n, m1);
+        stats.precond_used = ipm_pc;
         if (use64) start_point_t<double>(); else start_point_t<float>();
         int status = QP_EMAXIT;
         int k = 0;
@@ -1215,12 +1398,12 @@ public:
             ipm_k = k;
             // D = V^{-1}S, predictor r_c = S V e, r_a = r_i + V^{-1} r_c
             ipm_rc_kernel<<<vec_grid(m2), kVecThreads, 0, s>>>(m2, sl, nu, ri, nullptr, nullptr, 0.0, rc, ra, D64);
-            set_D(D64, pc);
+            set_D(D64, ipm_pc);
             // right-hand side of eq. [augmented]: -(r_g, r_e, r_a)
             axpby<double, double>(n, -1.0, rg, 0.0, fg, s);
             if (m1) axpby<double, double>(m1, -1.0, re, 0.0, fe, s);
             axpby<double, double>(m2, -1.0, ra, 0.0, fa, s);
-            int st_ = newton_solve(dxa, dla, dna, kind);
+            int st_ = newton_solve(dxa, dla, dna);
             if (st_ != QP_OK) { status = st_; break; }
             ipm_ds_kernel<<<vec_grid(m2), kVecThreads, 0, s>>>(m2, rc, nu, D64, dna, dsa);
             const double a_aff = std::min(1.0, max_step(sl, dsa, nu, dna));
@@ -1229,7 +1412,7 @@ public:
             // corrector: r_c = S V e + dS_aff dV_aff e - sigma mu e
             ipm_rc_kernel<<<vec_grid(m2), kVecThreads, 0, s>>>(m2, sl, nu, ri, dsa, dna, sigma * mu, rc, ra, nullptr);
             axpby<double, double>(m2, -1.0, ra, 0.0, fa, s);
-            st_ = newton_solve(dx, dl, dn, kind);
+            st_ = newton_solve(dx, dl, dn);
             if (st_ != QP_OK) { status = st_; break; }
             ipm_ds_kernel<<<vec_grid(m2), kVecThreads, 0, s>>>(m2, rc, nu, D64, dn, ds);
             const double alpha = std::min(1.0, tau * max_step(sl, ds, nu, dn));

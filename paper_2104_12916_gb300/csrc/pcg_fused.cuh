@@ -1,28 +1,40 @@
 // pcg_fused.cuh -- the PCG hot loop (a6-a10) as one persistent cooperative kernel.
 //
 // One launch runs every iteration of one PCG solve on K_F dnu = r_nu.  An
-// iteration is a chain of row-major matrix-vector phases (C' p, R^{-T} u,
-// Gt z1, Gt' z2, R^{-1} t, C y, then for P_H the two triangles of the inverse
-// factor of P~), separated by a grid barrier.
+// iteration is a chain of row-major matrix-vector phases separated by grid
+// barriers: u = C' p; the forward solve with the K0 factor L (stored as its
+// inverse: z1 = R^{-T} u and z2 = -Et u together, Et = L_S^{-1} A H^{-1} the
+// (2,1) block of L^{-1}); the back solve y = R^{-1} z1 + Et' z2; q = D p + C y;
+// then for P_H the two triangles of the inverse factor of P~.
 //
-// Layout of the work: a matrix is cut into chunks of 32 lanes x 8 x 16 bytes
-// (1024 FP32 or 512 FP64 elements) of one row; warps of the whole grid take
-// chunks round-robin and each lane keeps 8 independent 16-byte loads in flight.
-// Each chunk writes one partial sum; the next phase, while staging its input
-// vector into shared memory, adds a row's chunk partials in a fixed order and
-// applies the elementwise part of the method (D p, z1 + ..., the Jacobi
-// scaling, the PCG updates).  The PCG dot products (p'q, |r|^2, r'z) are summed
-// by every CTA over the whole vector in the same fixed order, so every CTA holds
-// bit-identical scalars without a reduction barrier.  Vectors read and written in
-// one phase (r, p) are double-buffered; each CTA writes only its own slice.
+// Layout of the work: a matrix is cut into chunks of 4 KB of one row (1024 FP32
+// or 512 FP64 elements).  Each block owns a contiguous range of the chunks of
+// every phase (rows next to each other in one chunk column).  The matrices do
+// not change during the solve, so their stream need not wait for the barriers:
+// a producer warp copies the block's chunks, phase after phase and iteration
+// after iteration, into a ring of shared-memory slots with bulk asynchronous
+// copies (cp.async.bulk, completion counted on one mbarrier per slot), running
+// ahead of the consumers by up to the ring's depth -- across the grid barriers,
+// where a kernel that only loads after the barrier leaves HBM idle.  The 15
+// consumer warps take the block's chunks in turn, dot them with the staged
+// vector and write one partial sum per chunk; the next phase, while staging its
+// input vector, adds a row's chunk partials in a fixed order and applies the
+// elementwise part of the method (D p, z1 + ..., the Jacobi scaling, the PCG
+// updates).  The PCG dot products (p'q, |r|^2, r'z) are summed by every block
+// over the whole vector in the same fixed order, so every block holds
+// bit-identical scalars without a reduction barrier.  Vectors read and written
+// in one phase (r, p) are double-buffered; each block writes only its own slice.
 //
-// Chunks that lie entirely outside a triangle are skipped (no load, no
+// Chunks that lie entirely outside a triangle are skipped (no copy, no
 // partial); inside a chunk, the zeros the triangle stores in memory are read.
 //
-// Every barrier wait is bounded: after kSpinLimit polls a block records
-// QP_ETIMEOUT in the barrier word and returns, and every other block returns at
-// its next barrier.
+// Every wait is bounded in time (kWaitNs on %globaltimer): a consumer that gives
+// up records QP_ETIMEOUT in the barrier word and every block returns at its next
+// grid barrier; the producer stops when the consumers stop (or its own wait
+// gives up) and then waits, again bounded, for the copies it has in flight.
 #pragma once
+
+#include <cstdint>
 
 #include "common.cuh"
 #include "dense.cuh"
@@ -30,12 +42,18 @@
 
 namespace pcgipm {
 
-constexpr int kFusedThreads = 512;
+constexpr int kFusedBlock = 512;                    // threads per block
+constexpr int kFusedThreads = kFusedBlock - 32;     // consumer threads (the last warp produces)
 constexpr int kFusedWarps = kFusedThreads / 32;
-constexpr unsigned long long kSpinLimit = 1ull << 25;   // ~ seconds with the 64 ns back-off
+constexpr int kSlotBytes = 4096;
+constexpr int kMaxSlots = 3 * kFusedWarps;       // ring depths are multiples of kFusedWarps
+constexpr int kMinSlots = kFusedWarps;
+constexpr int kSmallRingSlots = kFusedWarps;      // ring of a QP that shares the GPU
+constexpr int kMaxClusterBlocks = 16;             // grids up to this size launch as one cluster
+constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s bound on any wait
 
 struct GridBar {
-    unsigned int count;
+    unsigned int count;   // monotonic arrival counter (zeroed before each launch)
     unsigned int gen;
     int err;
     int pad;
@@ -46,8 +64,14 @@ struct GridBar {
 // SM, so an FP32 path must not touch FP64 arithmetic in its inner loops.)
 template <typename T> struct Acc { using type = T; };
 
-// Elements of one chunk for matrix element type T.
-template <typename T> struct Chunk { static constexpr int n = 32 * 8 * (16 / sizeof(T)); };
+// Elements of one chunk for matrix element type T (one 4 KB slot).
+template <typename T> struct Chunk { static constexpr int n = kSlotBytes / (int)sizeof(T); };
+
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
     unsigned v;
@@ -55,38 +79,113 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
     return v;
 }
 
-// Grid barrier: thread 0 of each block arrives with a release add on the counter;
-// the last arrival resets it and publishes the next generation with a release add;
-// the others poll the generation with acquire loads (bounded, see kSpinLimit).
-__device__ __forceinline__ bool grid_sync(GridBar* b, unsigned nblocks, int* s_flag) {
-    __syncthreads();
+// ---------------------------------------------------------------- mbarriers
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* b, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(b)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* b, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16);
+// completion is counted in bytes on `bar`.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Waits for the completion of the phase of parity `parity` of `b`; false after kWaitNs.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity) {
+    if (mbar_try_wait(b, parity)) return true;
+    const unsigned long long t0 = gtimer();
+    while (!mbar_try_wait(b, parity))
+        if (gtimer() - t0 > kWaitNs) return false;
+    return true;
+}
+
+// Ring of chunk slots in shared memory.  Slot s holds the chunks g with
+// g % S == s; its fill number is g / S.  full[s] completes one phase per copy
+// (producer arrival + transaction bytes), empty[s] one phase per consumption
+// (one arrival of the consuming warp).  A parity wait names the phase it waits
+// for exactly only while the waiter is at most one phase ahead, so every slot
+// has one owner on each side and each owner handles its slot's fills in order:
+//  - producer lane s % 32 issues every fill of slot s; before fill f it waits
+//    for the consumption of fill f - 1, and it had waited for that of f - 2
+//    before issuing f - 1;
+//  - S is a multiple of kFusedWarps and chunk g goes to consumer warp
+//    g % kFusedWarps, so slot s is always consumed by warp s % kFusedWarps,
+//    which has consumed fill f - 1 (hence seen it land) before it waits for f.
+// Neither side waits on anything but earlier chunks, so the ring cannot
+// deadlock.
+struct Ring {
+    unsigned char* buf;
+    uint64_t* full;
+    uint64_t* empty;
+    int* last_fill;          // per slot: fill number of the last copy issued, or -1
+    volatile int* stop;      // set by the consumers when they leave
+    int S;
+};
+
+// Named barrier of the consumer threads (the producer warp never joins it).
+__device__ __forceinline__ void csync() { asm volatile("bar.sync 1, %0;" ::"n"(kFusedThreads) : "memory"); }
+
+// Grid barrier over the consumers: thread 0 of each block adds 1 to a monotonic
+// counter (release) and polls it (acquire) until every block of this round has
+// arrived; `target` advances by the block count per barrier.  A wait failure
+// anywhere (`*err` of this block, a timeout here) is published in b->err and
+// makes every block's barrier return false.  Bounded by kWaitNs.
+__device__ __forceinline__ bool grid_sync(GridBar* b, unsigned nblocks, unsigned& target, const int* err,
+                                          int* s_flag) {
+    csync();
+    target += nblocks;
     if (threadIdx.x == 0) {
-        const unsigned g = ld_acquire(&b->gen);
-        unsigned arrived;
-        asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], 1;" : "=r"(arrived) : "l"(&b->count) : "memory");
-        if (arrived + 1u == nblocks) {
-            asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(&b->count) : "memory");
-            asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&b->gen) : "memory");
-        } else {
-            unsigned long long spins = 0;
-            while (ld_acquire(&b->gen) == g) {
-                if (++spins > kSpinLimit) {
+        if (*((volatile const int*)err)) atomicExch(&b->err, 2);
+        __threadfence();
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&b->count) : "memory");
+        if ((int)(ld_acquire(&b->count) - target) < 0) {
+            // poll with a short back-off: 152 blocks polling one word without it
+            // slow down the arrivals they wait for
+            const unsigned long long t0 = gtimer();
+            unsigned polls = 0;
+            while ((int)(ld_acquire(&b->count) - target) < 0) {
+                __nanosleep(32);
+                if ((++polls & 15) == 0 && gtimer() - t0 > kWaitNs) {
                     atomicExch(&b->err, 1);
                     break;
                 }
-                __nanosleep(32);
             }
         }
+        __threadfence();
         *s_flag = *((volatile int*)&b->err);
     }
-    __syncthreads();
+    csync();
     return *s_flag == 0;
 }
 
 // Items of a chunked GEMV phase: (row, chunk) pairs, chunk-column-major, with
 // the chunks that lie entirely outside a triangle left out so that the work is
-// spread evenly over the warps.  Chunk column c holds rows [r0(c), r1(c)):
-// all rows (TRI_NONE), rows >= c*CH (lower), rows < (c+1)*CH (upper).
+// spread evenly.  Chunk column c holds rows [r0(c), r1(c)): all rows
+// (TRI_NONE), rows >= c*CH (lower), rows < (c+1)*CH (upper).
 template <int TRI>
 __device__ __forceinline__ void chunk_rows(int c, int CH, int rows, int& r0, int& r1) {
     r0 = 0;
@@ -109,74 +208,86 @@ __device__ __forceinline__ long long chunk_items(int rows, int cols, int CH) {
 }
 
 // Item index -> (row, chunk).  `c`/`base` carry the last chunk column found so a
-// warp walking increasing item indices moves forward through the columns.
+// caller walking increasing item indices moves forward through the columns.
 template <int TRI>
 __device__ __forceinline__ void item_at(long long it, int rows, int nc, int CH, int& c, long long& base,
                                         int& row) {
     if constexpr (TRI == TRI_NONE) {
         c = (int)(it / rows);
         row = (int)(it - (long long)c * rows);
-        return;
-    }
-    while (true) {
-        int r0, r1;
-        chunk_rows<TRI>(c, CH, rows, r0, r1);
-        if (it < base + (r1 - r0) || c == nc - 1) {
-            row = r0 + (int)(it - base);
-            return;
+    } else {
+        while (true) {
+            int r0, r1;
+            chunk_rows<TRI>(c, CH, rows, r0, r1);
+            if (it < base + (r1 - r0) || c == nc - 1) {
+                row = r0 + (int)(it - base);
+                return;
+            }
+            base += r1 - r0;
+            ++c;
         }
-        base += r1 - r0;
-        ++c;
     }
 }
 
-// Hint the 4 KB chunk (row, c) into L2 (one 128-byte line per lane).
-template <typename TM>
-__device__ __forceinline__ void prefetch_chunk(const TM* M, long long ld, int row, int c, int cols) {
+// This block's contiguous item range [b0, b0 + cnt) of a phase.
+template <int TRI>
+__device__ __forceinline__ void block_range(int rows, int cols, int CH, long long& b0, long long& cnt) {
+    const long long nitems = chunk_items<TRI>(rows, cols, CH);
+    const long long per = (nitems + gridDim.x - 1) / gridDim.x;
+    b0 = (long long)blockIdx.x * per;
+    cnt = max(0LL, min(nitems, b0 + per) - b0);
+}
+
+// Producer side of one phase: each lane copies the items whose slot it owns, in
+// increasing order.  `g0` is the ring sequence number of the phase's first item
+// (advanced by the item count).  Returns false (in every lane) once the
+// consumers have stopped or a wait gave up.
+template <typename TM, int TRI>
+__device__ __forceinline__ bool produce_phase(const TM* __restrict__ M, int rows, int cols, long long ld,
+                                              const Ring& R, long long& g0) {
     constexpr int CH = Chunk<TM>::n;
     const int lane = threadIdx.x & 31;
-    const long long e = (long long)c * CH + (long long)lane * (128 / sizeof(TM));
-    if (e < ld) {
-        const TM* addr = M + (long long)row * ld + e;
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(addr));
-    }
-}
-
-// L2 hint of this warp's first item of a coming phase (issued before a barrier),
-// with the item assignment of gemv_chunks.
-template <typename TM, int TRI>
-__device__ __forceinline__ void prefetch_first(const TM* M, int rows, int cols, long long ld, int flags = 0) {
-    constexpr int CH = Chunk<TM>::n;
-    const int warp = threadIdx.x >> 5;
     const int nc = (cols + CH - 1) / CH;
-    const long long nitems = chunk_items<TRI>(rows, cols, CH);
-    long long first, last;
-    if (flags & 2) {
-        first = blockIdx.x * kFusedWarps + warp;
-        last = nitems;
-    } else {
-        const long long per = (nitems + gridDim.x - 1) / gridDim.x;
-        first = (long long)blockIdx.x * per + warp;
-        last = min(nitems, (long long)blockIdx.x * per + per);
-    }
-    if (first >= last || (flags & 4)) return;
+    long long b0, cnt;
+    block_range<TRI>(rows, cols, CH, b0, cnt);
     int c = 0, row = 0;
     long long base = 0;
-    item_at<TRI>(first, rows, nc, CH, c, base, row);
-    prefetch_chunk<TM>(M, ld, row, c, cols);
+    bool ok = true;
+    int slot = (int)(g0 % R.S);
+    int fill = (int)(g0 / R.S);
+    for (long long i = 0; i < cnt; ++i, ++slot) {
+        if (slot == R.S) { slot = 0; ++fill; }
+        if ((slot & 31) != lane) continue;
+        if (*R.stop) { ok = false; break; }
+        item_at<TRI>(b0 + i, rows, nc, CH, c, base, row);
+        if (fill > 0) {
+            // the slot is free once its previous chunk has been consumed
+            const unsigned par = (unsigned)((fill - 1) & 1);
+            bool got = mbar_try_wait(&R.empty[slot], par);
+            if (!got) {
+                const unsigned long long t0 = gtimer();
+                while (!(got = mbar_try_wait(&R.empty[slot], par)))
+                    if (*R.stop || gtimer() - t0 > kWaitNs) break;
+            }
+            if (!got) { ok = false; break; }
+        }
+        const long long e0 = (long long)c * CH;
+        const unsigned bytes = (unsigned)(min((long long)CH, ld - e0) * (long long)sizeof(TM));
+        R.last_fill[slot] = fill;
+        mbar_expect_tx(&R.full[slot], bytes);
+        bulk_g2s(R.buf + (size_t)slot * kSlotBytes, M + (long long)row * ld + e0, bytes, &R.full[slot]);
+    }
+    g0 += cnt;
+    return __all_sync(0xffffffffu, ok);
 }
 
-// Chunked GEMV phase: part[c * pld + row] = sum over chunk c of row `row` of M . xs
-// (chunk-major, so that the consumer's per-row sums load coalesced).
-// TRI: TRI_NONE / TRI_LOWER (square) / TRI_UPPER (square).
-// Each block takes a contiguous range of items (rows next to each other in one
-// chunk column: few pages, sequential DRAM rows) and its warps interleave
-// within it.  flags bit 0: no L2 prefetch of the next item; bit 1: round-robin
-// items over all warps of the grid instead.
+// Consumer side of one phase: part[c * pld + row] = chunk c of row `row` of M . xs
+// (chunk-major, so that the next phase's per-row sums load coalesced).  Warp w
+// takes the items whose ring sequence number g is w modulo kFusedWarps.
 template <typename TM, int TRI>
-__device__ __forceinline__ void gemv_chunks(const TM* __restrict__ M, int rows, int cols, long long ld,
-                                            const TM* __restrict__ xs, TM* __restrict__ part, int pld,
-                                            int flags = 0) {
+__device__ __forceinline__ void gemv_ring(const Ring& R, long long& g0, int rows, int cols, long long ld,
+                                          const TM* __restrict__ xs, TM* __restrict__ part, int pld,
+                                          int* err) {
     using VT = Vec16<TM>;
     using V = typename VT::type;
     constexpr int CH = Chunk<TM>::n;
@@ -184,50 +295,38 @@ __device__ __forceinline__ void gemv_chunks(const TM* __restrict__ M, int rows, 
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int nc = (cols + CH - 1) / CH;
-    const long long nitems = chunk_items<TRI>(rows, cols, CH);
-    long long first, step, last;
-    if (flags & 2) {
-        first = blockIdx.x * kFusedWarps + warp;
-        step = (long long)gridDim.x * kFusedWarps;
-        last = nitems;
-    } else {
-        const long long per = (nitems + gridDim.x - 1) / gridDim.x;
-        const long long b0 = (long long)blockIdx.x * per;
-        first = b0 + warp;
-        step = kFusedWarps;
-        last = min(nitems, b0 + per);
-    }
+    long long b0, cnt;
+    block_range<TRI>(rows, cols, CH, b0, cnt);
     const V* xv = reinterpret_cast<const V*>(xs);
     int c = 0, row = 0;
     long long base = 0;
-    if (first < last) item_at<TRI>(first, rows, nc, CH, c, base, row);
-    for (long long it = first; it < last; it += step) {
-        const int crow = row, cc = c;
-        // locate (and L2-prefetch) the next item while this one loads
-        if (it + step < last) {
-            item_at<TRI>(it + step, rows, nc, CH, c, base, row);
-            if (!(flags & 1)) prefetch_chunk<TM>(M, ld, row, c, cols);
-        }
-        const V* mr = reinterpret_cast<const V*>(M + (long long)crow * ld + (long long)cc * CH);
-        const int vbase = cc * (CH / VN);
-        const int vend = (int)(ld / VN) - vbase;   // vectors of this row left from the chunk start
-        V a[8];
+    const long long first = (long long)((warp - (int)(g0 % kFusedWarps) + kFusedWarps) % kFusedWarps);
+    for (long long i = first; i < cnt; i += kFusedWarps) {
+        item_at<TRI>(b0 + i, rows, nc, CH, c, base, row);
+        const int vbase = c * (CH / VN);
+        const long long g = g0 + i;
+        const int slot = (int)(g % R.S);
+        if (!mbar_wait(&R.full[slot], (unsigned)((g / R.S) & 1))) *err = 1;
+        const V* sv = reinterpret_cast<const V*>(R.buf + (size_t)slot * kSlotBytes);
+        const int vend = (int)(ld / VN) - vbase;   // vectors of this row from the chunk start
+        TM acc = TM(0);
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             const int v = lane + 32 * k;
-            a[k] = (v < vend) ? __ldg(mr + v) : V{};
+            const V m = (v < vend) ? sv[v] : V{};
+            acc = VT::dot(m, xv[vbase + v], acc);
         }
-        TM acc = TM(0);
-#pragma unroll
-        for (int k = 0; k < 8; ++k) acc = VT::dot(a[k], xv[vbase + lane + 32 * k], acc);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&R.empty[slot]);
         acc = warp_sum(acc);
-        if (lane == 0) part[(long long)cc * pld + crow] = acc;
+        if (lane == 0) part[(long long)c * pld + row] = acc;
     }
+    g0 += cnt;
 }
 
 // Chunk sums of four rows j[0..3] at once (rows >= len give 0): for each row the
-// chunks are added in increasing order (the same order as row_total), but the
-// loads of all four rows and four consecutive chunks are issued together.
+// chunks are added in increasing order, the loads of all four rows and four
+// consecutive chunks issued together.
 template <typename TM, int TRI, typename AT>
 __device__ __forceinline__ void sum_chunks4(const TM* __restrict__ part, int pld, int cols, const int* j,
                                             int len, AT* out) {
@@ -264,7 +363,7 @@ __device__ __forceinline__ void sum_chunks4(const TM* __restrict__ part, int pld
 }
 
 // Stage xs[j] for j < pad (zero from len on): rows are taken four per thread;
-// f(j4, valid, s4, val4) turns the four chunk sums into the four values.
+// f(j, sum) turns a row's chunk sum into the staged value.
 template <typename TX, typename TM, int TRI, class F>
 __device__ __forceinline__ void stage_sum(TX* xs, const TM* part, int pld, int cols, int len, int pad, F f) {
     using AT = typename Acc<TM>::type;
@@ -280,21 +379,21 @@ __device__ __forceinline__ void stage_sum(TX* xs, const TM* part, int pld, int c
     }
 }
 
-// Block-wide fixed-order sum, result broadcast to every thread.
+// Consumer-wide fixed-order sum, result broadcast to every consumer thread.
 template <typename AT>
 __device__ __forceinline__ AT block_allsum(AT v, AT* sh) {
     v = warp_sum(v);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     if (l == 0) sh[w] = v;
-    __syncthreads();
+    csync();
     if (threadIdx.x < 32) {
         AT r = (l < kFusedWarps) ? sh[l] : AT(0);
         r = warp_sum(r);
         if (l == 0) sh[32] = r;
     }
-    __syncthreads();
+    csync();
     v = sh[32];
-    __syncthreads();
+    csync();
     return v;
 }
 
@@ -302,8 +401,8 @@ template <typename TO, typename TP>
 struct FusedArgs {
     int n, m1, m2;
     // operator (precision TO)
-    const TO *CWT, *WH, *Gt, *GtT, *WHT, *CW;
-    long long ldCWT, ldWH, ldGt, ldGtT, ldWHT, ldCW;
+    const TO *CWT, *WH, *Et, *EtT, *WHT, *CW;
+    long long ldCWT, ldWH, ldEt, ldEtT, ldWHT, ldCW;
     // preconditioner (precision TP)
     const TP *WPl, *WPu;
     long long ldWP;
@@ -318,49 +417,121 @@ struct FusedArgs {
     TP *PV, *PZ;
     int ldU, ldZ1, ldZ2, ldT, ldY, ldQ, ldV, ldZ;
     PcgState* st;      // entry: rz_cur, tol2, maxit, done (from pcg_init); exit: iter, rr, done
-    GridBar* bar;
+    GridBar* bar;      // zeroed before the launch
     size_t xs_bytes;   // bytes of the staged-vector region of shared memory (16-byte multiple)
+    size_t ring_off;   // byte offset of the slot ring (128-byte aligned)
+    int slots;         // ring depth S
     unsigned long long* tstamp;   // optional: %globaltimer at phase marks of the first 4 iterations
-    int flags;                    // bit 0: no next-item L2 prefetch; bit 1: round-robin items; bit 2: no
-                                  // prefetch of the next phase before a barrier
 };
+
+// Shared-memory layout of the persistent kernel: staged vector, three m2-vector
+// caches, then the ring (slots, full and empty mbarriers, last-fill words, stop flag).
+template <typename TO>
+inline size_t fused_ring_offset(size_t xs_bytes, int m2) {
+    const size_t o = xs_bytes + 3 * (size_t)m2 * sizeof(TO);
+    return (o + 127) / 128 * 128;
+}
+inline size_t fused_smem_bytes(size_t ring_off, int slots) {
+    return ring_off + (size_t)slots * (kSlotBytes + 2 * sizeof(uint64_t) + sizeof(int)) + 16;
+}
+
+// The producer's sequence of phases, the consumers' loop below in the same order.
+template <typename TO, typename TP, int PC>
+__device__ void pcg_producer(const FusedArgs<TO, TP>& a, const Ring& R) {
+    const int n = a.n, m1 = a.m1, m2 = a.m2;
+    long long g = 0;
+    while (!*R.stop) {   // (a block may own no chunk of any phase: it polls the stop flag here)
+        if (!produce_phase<TO, TRI_NONE>(a.CWT, n, m2, a.ldCWT, R, g)) break;
+        if (!produce_phase<TO, TRI_LOWER>(a.WH, n, n, a.ldWH, R, g)) break;
+        if (m1 > 0 && !produce_phase<TO, TRI_NONE>(a.Et, m1, n, a.ldEt, R, g)) break;
+        if (!produce_phase<TO, TRI_UPPER>(a.WHT, n, n, a.ldWHT, R, g)) break;
+        if (m1 > 0 && !produce_phase<TO, TRI_NONE>(a.EtT, n, m1, a.ldEtT, R, g)) break;
+        if (!produce_phase<TO, TRI_NONE>(a.CW, m2, n, a.ldCW, R, g)) break;
+        if (PC == PC_H_K) {
+            if (!produce_phase<TP, TRI_LOWER>(a.WPl, m2, m2, a.ldWP, R, g)) break;
+            if (!produce_phase<TP, TRI_UPPER>(a.WPu, m2, m2, a.ldWP, R, g)) break;
+        }
+    }
+    // drain: every copy issued lands before the block's shared memory goes away
+    __syncwarp();
+    const int lane = threadIdx.x & 31;
+    for (int sl = lane; sl < R.S; sl += 32) {
+        const int f = R.last_fill[sl];
+        if (f >= 0) mbar_wait(&R.full[sl], (unsigned)(f & 1));
+    }
+}
 
 // kind: PC_L_K (z = r / D), PC_H_K (z = Sg W' W Sg r), PC_NONE_K (z = r).
 // Entry state (from pcg_init): x = 0, r = r0 = rhs, p = p0 = z0, st->rz_cur = r'z,
 // st->tol2 = tol^2 |rhs|^2, st->maxit.  Shared memory: the staged vector
-// (xs_bytes) followed by three m2-vectors in TO: q = K_F p, r and p of the
-// current iteration.
+// (xs_bytes), three m2-vectors in TO (q = K_F p, r and p of the current
+// iteration), then the ring.
 template <typename TO, typename TP, int PC>
-__global__ void __launch_bounds__(kFusedThreads, 1) pcg_fused_kernel(const FusedArgs<TO, TP> a) {
+__global__ void __launch_bounds__(kFusedBlock, 1) pcg_fused_kernel(const FusedArgs<TO, TP> a) {
     PCG_COUNT_KERNEL();
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    TO* xs = reinterpret_cast<TO*>(smem_raw);
-    TP* xp = reinterpret_cast<TP*>(smem_raw);
-    TO* qc = reinterpret_cast<TO*>(smem_raw + a.xs_bytes);
+    extern __shared__ __align__(128) unsigned char pcg_smem[];
+    TO* xs = reinterpret_cast<TO*>(pcg_smem);
+    TP* xp = reinterpret_cast<TP*>(pcg_smem);
+    TO* qc = reinterpret_cast<TO*>(pcg_smem + a.xs_bytes);
     TO* rc = qc + a.m2;
     TO* pcs = rc + a.m2;
+    Ring R;
+    R.S = a.slots;
+    R.buf = pcg_smem + a.ring_off;
+    R.full = reinterpret_cast<uint64_t*>(R.buf + (size_t)R.S * kSlotBytes);
+    R.empty = R.full + R.S;
+    R.last_fill = reinterpret_cast<int*>(R.empty + R.S);
+    R.stop = reinterpret_cast<volatile int*>(R.last_fill + R.S);
     using AT = typename Acc<TO>::type;
     __shared__ AT sh[40];
     __shared__ int s_flag;
+    __shared__ int s_err;
     const int n = a.n, m1 = a.m1, m2 = a.m2;
     const int tid = threadIdx.x;
     const unsigned nblocks = gridDim.x;
+
+    if (__ldcg(&a.st->done)) return;
+    if (tid == 0) {
+        for (int sl = 0; sl < R.S; ++sl) {
+            mbar_init(&R.full[sl], 1);
+            mbar_init(&R.empty[sl], 1);
+            R.last_fill[sl] = -1;
+        }
+        *R.stop = 0;
+        s_err = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid >= kFusedThreads) {
+        pcg_producer<TO, TP, PC>(a, R);
+        return;
+    }
+
+    // ------------------------------------------------------------ consumers
     // slice of the m2-vectors this block owns for writes
     const int per = (m2 + nblocks - 1) / nblocks;
     const int own0 = blockIdx.x * per, own1 = min(m2, own0 + per);
     constexpr int CHO = Chunk<TO>::n, CHP = Chunk<TP>::n;
     const int padO_n = ((n + CHO - 1) / CHO) * CHO, padO_m2 = ((m2 + CHO - 1) / CHO) * CHO;
     const int padO_m1 = ((m1 + CHO - 1) / CHO) * CHO, padP_m2 = ((m2 + CHP - 1) / CHP) * CHP;
+    TO* xs2 = xs + padO_n;   // z2, beside z1, for the back solve
     const bool stamp = a.tstamp != nullptr && blockIdx.x == 0 && tid == 0;
     auto mark = [&](int it, int ph) {
-        if (stamp && it < 4) {
-            unsigned long long t;
-            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-            a.tstamp[it * 32 + ph] = t;
+        if (stamp && it < 4) a.tstamp[it * 32 + ph] = gtimer();
+    };
+    unsigned target = 0;
+    long long g = 0;   // ring sequence number of the next chunk
+    // every consumer exit passes here: the producer stops issuing and drains
+    auto leave = [&]() {
+        csync();
+        if (tid == 0) {
+            if (s_err) atomicExch(&a.bar->err, 2);
+            *R.stop = 1;
         }
     };
+    auto gsync = [&]() { return grid_sync(a.bar, nblocks, target, &s_err, &s_flag); };
 
-    if (__ldcg(&a.st->done)) return;
     AT rz = (AT)__ldcg(&a.st->rz_cur);
     const double tol2 = __ldcg(&a.st->tol2);
     const int maxit = __ldcg(&a.st->maxit);
@@ -375,76 +546,57 @@ __global__ void __launch_bounds__(kFusedThreads, 1) pcg_fused_kernel(const Fused
         pcs[j] = __ldcg(pc + j);
         rc[j] = __ldcg(rcur + j);
     }
-    __syncthreads();
+    csync();
     for (int j = tid; j < padO_m2; j += kFusedThreads) xs[j] = (j < m2) ? pcs[j] : TO(0);
-    __syncthreads();
+    csync();
 
     while (true) {
         mark(it, 0);
         // ---- P1 (a6): u = C' p
-        gemv_chunks<TO, TRI_NONE>(a.CWT, n, m2, a.ldCWT, xs, a.PU, a.ldU, a.flags);
+        gemv_ring<TO, TRI_NONE>(R, g, n, m2, a.ldCWT, xs, a.PU, a.ldU, &s_err);
         mark(it, 11);
-        prefetch_first<TO, TRI_LOWER>(a.WH, n, n, a.ldWH, a.flags);
-        if (!grid_sync(a.bar, nblocks, &s_flag)) return;
+        if (!gsync()) { leave(); return; }
         mark(it, 1);
-        // ---- P2 (a7): z1 = R^{-T} u
+        // ---- P2 (a7, forward solve with L): z1 = R^{-T} u, Et u (z2 = -Et u)
         stage_sum<TO, TO, TRI_NONE>(xs, a.PU, a.ldU, m2, n, padO_n, [&](int, AT v) { return (TO)v; });
-        __syncthreads();
+        csync();
         mark(it, 12);
-        gemv_chunks<TO, TRI_LOWER>(a.WH, n, n, a.ldWH, xs, a.PZ1, a.ldZ1, a.flags);
+        gemv_ring<TO, TRI_LOWER>(R, g, n, n, a.ldWH, xs, a.PZ1, a.ldZ1, &s_err);
+        if (m1 > 0) gemv_ring<TO, TRI_NONE>(R, g, m1, n, a.ldEt, xs, a.PZ2, a.ldZ2, &s_err);
         mark(it, 13);
-        if (m1 > 0) prefetch_first<TO, TRI_NONE>(a.Gt, m1, n, a.ldGt, a.flags);
-        else prefetch_first<TO, TRI_UPPER>(a.WHT, n, n, a.ldWHT, a.flags);
-        if (!grid_sync(a.bar, nblocks, &s_flag)) return;
+        if (!gsync()) { leave(); return; }
         mark(it, 2);
-        if (m1 > 0) {
-            // ---- P3: z2 = -Gt z1
-            stage_sum<TO, TO, TRI_LOWER>(xs, a.PZ1, a.ldZ1, n, n, padO_n, [&](int, AT v) { return (TO)v; });
-            __syncthreads();
-            gemv_chunks<TO, TRI_NONE>(a.Gt, m1, n, a.ldGt, xs, a.PZ2, a.ldZ2, a.flags);
-            prefetch_first<TO, TRI_NONE>(a.GtT, n, m1, a.ldGtT, a.flags);
-            if (!grid_sync(a.bar, nblocks, &s_flag)) return;
-            mark(it, 3);
-            // ---- P4: t = z1 + Gt' z2
-            stage_sum<TO, TO, TRI_NONE>(xs, a.PZ2, a.ldZ2, n, m1, padO_m1, [&](int, AT v) { return (TO)(-v); });
-            __syncthreads();
-            gemv_chunks<TO, TRI_NONE>(a.GtT, n, m1, a.ldGtT, xs, a.PT, a.ldT, a.flags);
-            prefetch_first<TO, TRI_UPPER>(a.WHT, n, n, a.ldWHT, a.flags);
-            if (!grid_sync(a.bar, nblocks, &s_flag)) return;
-            mark(it, 4);
-        }
-        // ---- P5: y = R^{-1} t
-        // t = z1 + Gt' z2: the Gt' partials first (into xs), then z1 added on top
+        // ---- P3 (a7, back solve with L'): y = R^{-1} z1 + Et' z2
+        stage_sum<TO, TO, TRI_LOWER>(xs, a.PZ1, a.ldZ1, n, n, padO_n, [&](int, AT v) { return (TO)v; });
+        if (m1 > 0)
+            stage_sum<TO, TO, TRI_NONE>(xs2, a.PZ2, a.ldZ2, n, m1, padO_m1, [&](int, AT v) { return (TO)(-v); });
+        csync();
+        mark(it, 14);
+        gemv_ring<TO, TRI_UPPER>(R, g, n, n, a.ldWHT, xs, a.PY, a.ldY, &s_err);
+        if (m1 > 0) gemv_ring<TO, TRI_NONE>(R, g, n, m1, a.ldEtT, xs2, a.PT, a.ldT, &s_err);
+        mark(it, 15);
+        if (!gsync()) { leave(); return; }
+        mark(it, 5);
+        // ---- P4 (a8): q = D p + C y
         if (m1 > 0) {
             stage_sum<TO, TO, TRI_NONE>(xs, a.PT, a.ldT, m1, n, padO_n, [&](int, AT v) { return (TO)v; });
-            __syncthreads();
-            stage_sum<TO, TO, TRI_LOWER>(xs, a.PZ1, a.ldZ1, n, n, padO_n,
+            csync();
+            stage_sum<TO, TO, TRI_UPPER>(xs, a.PY, a.ldY, n, n, padO_n,
                                          [&](int j, AT v) { return (TO)(v + (AT)xs[j]); });
         } else {
-            stage_sum<TO, TO, TRI_LOWER>(xs, a.PZ1, a.ldZ1, n, n, padO_n, [&](int, AT v) { return (TO)v; });
+            stage_sum<TO, TO, TRI_UPPER>(xs, a.PY, a.ldY, n, n, padO_n, [&](int, AT v) { return (TO)v; });
         }
-        __syncthreads();
-        mark(it, 14);
-        gemv_chunks<TO, TRI_UPPER>(a.WHT, n, n, a.ldWHT, xs, a.PY, a.ldY, a.flags);
-        mark(it, 15);
-        prefetch_first<TO, TRI_NONE>(a.CW, m2, n, a.ldCW, a.flags);
-        if (!grid_sync(a.bar, nblocks, &s_flag)) return;
-        mark(it, 5);
-        // ---- P6 (a8): q = D p + C y
-        stage_sum<TO, TO, TRI_UPPER>(xs, a.PY, a.ldY, n, n, padO_n, [&](int, AT v) { return (TO)v; });
-        __syncthreads();
+        csync();
         mark(it, 16);
-        gemv_chunks<TO, TRI_NONE>(a.CW, m2, n, a.ldCW, xs, a.PQ, a.ldQ, a.flags);
+        gemv_ring<TO, TRI_NONE>(R, g, m2, n, a.ldCW, xs, a.PQ, a.ldQ, &s_err);
         mark(it, 17);
-        if (PC == PC_H_K) prefetch_first<TP, TRI_LOWER>(a.WPl, m2, m2, a.ldWP, a.flags);
-        else prefetch_first<TO, TRI_NONE>(a.CWT, n, m2, a.ldCWT, a.flags);
-        if (!grid_sync(a.bar, nblocks, &s_flag)) return;
+        if (!gsync()) { leave(); return; }
         mark(it, 6);
 
-        // ---- P7 (a10): q = D p + C y (cached), alpha = r'z / p'q, x += alpha p, r -= alpha q
+        // ---- P5 (a10): q = D p + C y (cached), alpha = r'z / p'q, x += alpha p, r -= alpha q
         stage_sum<TO, TO, TRI_NONE>(qc, a.PQ, a.ldQ, n, m2, m2,
                                     [&](int j, AT v) { return (TO)fma((AT)__ldg(a.D + j), (AT)pcs[j], v); });
-        __syncthreads();
+        csync();
         AT pq = AT(0);
         for (int j = tid; j < m2; j += kFusedThreads) pq = fma((AT)pcs[j], (AT)qc[j], pq);
         pq = block_allsum(pq, sh);
@@ -484,25 +636,23 @@ __global__ void __launch_bounds__(kFusedThreads, 1) pcg_fused_kernel(const Fused
 
         AT rz_new;
         if (PC == PC_H_K) {
-            __syncthreads();
-            // ---- P8 (a9): v = W rs, z = Sg W' v
-            gemv_chunks<TP, TRI_LOWER>(a.WPl, m2, m2, a.ldWP, xp, a.PV, a.ldV, a.flags);
+            csync();
+            // ---- P6 (a9): v = W rs, z = Sg W' v
+            gemv_ring<TP, TRI_LOWER>(R, g, m2, m2, a.ldWP, xp, a.PV, a.ldV, &s_err);
             mark(it - 1, 18);
-            prefetch_first<TP, TRI_UPPER>(a.WPu, m2, m2, a.ldWP, a.flags);
-            if (!grid_sync(a.bar, nblocks, &s_flag)) return;
+            if (!gsync()) { leave(); return; }
             mark(it - 1, 8);
             stage_sum<TP, TP, TRI_LOWER>(xp, a.PV, a.ldV, m2, m2, padP_m2, [&](int, typename Acc<TP>::type v) { return (TP)v; });
-            __syncthreads();
+            csync();
             mark(it - 1, 19);
-            gemv_chunks<TP, TRI_UPPER>(a.WPu, m2, m2, a.ldWP, xp, a.PZ, a.ldZ, a.flags);
+            gemv_ring<TP, TRI_UPPER>(R, g, m2, m2, a.ldWP, xp, a.PZ, a.ldZ, &s_err);
             mark(it - 1, 20);
-            prefetch_first<TO, TRI_NONE>(a.CWT, n, m2, a.ldCWT, a.flags);
-            if (!grid_sync(a.bar, nblocks, &s_flag)) return;
+            if (!gsync()) { leave(); return; }
             mark(it - 1, 9);
             // z into the q cache (q is no longer needed), then r'z
             stage_sum<TO, TP, TRI_UPPER>(qc, a.PZ, a.ldZ, m2, m2, m2,
                                          [&](int j, typename Acc<TP>::type v) { return (TO)((AT)__ldg(a.sg + j) * (AT)v); });
-            __syncthreads();
+            csync();
             rzp = AT(0);
             for (int j = tid; j < m2; j += kFusedThreads) rzp = fma((AT)rc[j], (AT)qc[j], rzp);
             rz_new = block_allsum(rzp, sh);
@@ -525,7 +675,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) pcg_fused_kernel(const Fused
             }
             xs[j] = v;
         }
-        __syncthreads();
+        csync();
         mark(it - 1, 10);
         // swap the double buffers (global copies; the shared caches already hold the new values)
         TO* t1 = pc; pc = pn; pn = t1;
@@ -537,6 +687,7 @@ __global__ void __launch_bounds__(kFusedThreads, 1) pcg_fused_kernel(const Fused
         a.st->rz_cur = (double)rz;
         a.st->done = done;
     }
+    leave();
 }
 
 }  // namespace pcgipm

@@ -81,12 +81,13 @@ void qp_opts_default(qp_opts* o) {
     o->stream = nullptr;
 }
 
-int qp_create(qp_t* out, int n, int m1, int m2, const double* H, const double* c, const double* A,
-              const double* b, const double* C, const double* d, const qp_opts* opts, int ptr_kind) {
+static int create_common(qp_t* out, int n, int m1, int m2, const double* H, const double* c, const double* A,
+                         const double* b, const double* C, const Engine::CsrIn* csr, const double* d,
+                         const qp_opts* opts, int ptr_kind) {
     if (!out) return QP_EINVAL;
     *out = nullptr;
     if (n < 1 || m1 < 0 || m1 > n || m2 < 1) return QP_EINVAL;
-    if (!H || !c || !C || !d || (m1 > 0 && (!A || !b))) return QP_EINVAL;
+    if (!H || !c || (!C && !csr) || !d || (m1 > 0 && (!A || !b))) return QP_EINVAL;
     if (ptr_kind != QP_PTR_HOST && ptr_kind != QP_PTR_DEVICE) return QP_EINVAL;
     qp_opts o;
     qp_opts_default(&o);
@@ -96,10 +97,35 @@ int qp_create(qp_t* out, int n, int m1, int m2, const double* H, const double* c
     return guarded([&]() {
         std::unique_ptr<qp_s> h(new qp_s);
         h->eng.reset(new Engine(n, m1, m2, o));
-        h->eng->load(H, c, A, b, C, d, ptr_kind);
+        h->eng->load(H, c, A, b, C, d, ptr_kind, csr);
         *out = h.release();
         return QP_OK;
     });
+}
+
+int qp_create(qp_t* out, int n, int m1, int m2, const double* H, const double* c, const double* A,
+              const double* b, const double* C, const double* d, const qp_opts* opts, int ptr_kind) {
+    if (!C) return QP_EINVAL;
+    return create_common(out, n, m1, m2, H, c, A, b, C, nullptr, d, opts, ptr_kind);
+}
+
+int qp_create_csr(qp_t* out, int n, int m1, int m2, const double* H, const double* c, const double* A,
+                  const double* b, const int* C_rowptr, const int* C_colidx, const double* C_val,
+                  const double* d, const qp_opts* opts, int ptr_kind) {
+    if (!C_rowptr || !C_colidx || !C_val) {
+        if (out) *out = nullptr;
+        return QP_EINVAL;
+    }
+    const Engine::CsrIn csr{C_rowptr, C_colidx, C_val};
+    return create_common(out, n, m1, m2, H, c, A, b, nullptr, &csr, d, opts, ptr_kind);
+}
+
+size_t qp_device_bytes_bound(int n, int m1, int m2, const qp_opts* opts) {
+    if (n < 1 || m1 < 0 || m1 > n || m2 < 1) return 0;
+    qp_opts o;
+    qp_opts_default(&o);
+    if (opts) o = *opts;
+    return Engine::bytes_bound(n, m1, m2, o);
 }
 
 int qp_factor_K0(qp_t qp) {
@@ -198,6 +224,8 @@ int qp_batch_solve(qp_t* qps, int count, int max_concurrent, qp_result* results)
             r.res_p = e->stats.res_p;
             r.res_d = e->stats.res_d;
             r.mu = e->stats.mu;
+            r.wait_ms = 0.0;
+            r.latency_ms = r.solve_ms;
             results[i] = r;
         }
     };

@@ -328,6 +328,30 @@ __global__ void diag_rsqrt_kernel(int n, const double* __restrict__ H, long long
         hs[i] = 1.0 / sqrt(H[i * ld + i]);
 }
 
+// Dense expansion of a CSR matrix into a zeroed row-major array (one thread per
+// row, entries added in storage order, so repeated columns are summed the same
+// way every time).  A bad row pointer or column index sets *bad.
+__global__ void csr_scatter_kernel(int rows, int cols, long long nnz, const int* __restrict__ rowptr,
+                                   const int* __restrict__ colidx, const double* __restrict__ val,
+                                   double* __restrict__ M, long long ld, int* bad) {
+    PCG_COUNT_KERNEL();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= rows) return;
+    const long long k0 = rowptr[i], k1 = rowptr[i + 1];
+    if ((i == 0 && k0 != 0) || k0 < 0 || k1 < k0 || k1 > nnz) {
+        atomicAdd(bad, 1);
+        return;
+    }
+    for (long long k = k0; k < k1; ++k) {
+        const int j = colidx[k];
+        if (j < 0 || j >= cols) {
+            atomicAdd(bad, 1);
+            continue;
+        }
+        M[(long long)i * ld + j] += val[k];
+    }
+}
+
 // Count of non-finite entries (for input validation), added to *bad.
 __global__ void nonfinite_kernel(long long n, const double* __restrict__ v, int* bad) {
     PCG_COUNT_KERNEL();

@@ -58,3 +58,24 @@ def test_batch_matches_oracle_and_alone(B, prec):
         x = np.zeros(q.n)
         B.qp_ipm_solve(h.h, x)
         assert np.array_equal(x, xb), q.name
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_auto_moves_from_pl_to_ph_when_pl_stops_converging(B, prec):
+    """A QP of the batched recipe at the tie 2 m1 = n (AUTO picks P_L) whose late
+    IPM iterations take D over 18 decades: the P_L-preconditioned spectrum
+    1 + lambda(X) grows without bound (Sec. 4.3, Theorem 1) and PCG stops
+    converging, so AUTO moves the QP to P_H."""
+    q = qpgen.batch_qp(201)
+    assert 2 * q.m1 == q.n
+    ref = ipm.solve_qp(q, variant="kkt3")
+    o = B.qp_opts_default()
+    o.precision = prec
+    h = B.QP.from_qpgen(q, o)
+    st, f, its, _ = B.qp_ipm_solve(h.h)
+    assert st == B.QP_OK
+    stats = B.qp_get_stats(h.h)
+    assert stats["pc_switch_iter"] >= 0 and stats["precond_used"] == B.QP_PC_PH_EXACT, stats
+    assert abs(f - ref.f) / max(abs(ref.f), 1.0) <= 1e-9
+    assert abs(its - ref.iters) <= 2
+    h.close()
