@@ -65,6 +65,20 @@ def dist_env():
     return world, rank, local
 
 
+def reduce_over_ranks(total_ms, solved, device=None):
+    """Whole-job figures of a replicated run: the slowest rank's timed total and
+    the QPs solved by all ranks (a no-op without torch.distributed)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(total_ms), int(solved)
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    k = torch.tensor([int(solved)], dtype=torch.int64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(k, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(k.item())
+
+
 # ---------------------------------------------------------------- CPU baseline
 def oracle_sample(qp, ipm_iters_full, sample_iters=2):
     """Time the FP64 oracle (3x3 LDL^T variant) on a bounded sample of the same
@@ -201,21 +215,16 @@ def run_ours(args):
             total_ms += e0.elapsed_time(e1)
         barrier()
         launches = B.qp_kernel_launches() - l0
-        if world > 1:
-            import torch.distributed as dist
-            tt = torch.tensor([total_ms], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            total_ms = float(tt.item())
         ok = [abs(r["f"] - gold["f"]) / max(abs(gold["f"]), 1.0) <= 1e-6 and r["status"] == 0 for r in res]
-        return res, total_ms, ok, launches
+        total_ms, solved_all = reduce_over_ranks(total_ms, sum(ok), dev)
+        return res, total_ms, ok, launches, solved_all
 
     with ClockSampler(local) as clk:
-        res, total_ms, ok, launches = timed(B.QP_PREC_FP32, args.steps, args.warmup)
-    res64, total64, ok64, _ = timed(B.QP_PREC_FP64, args.fp64_steps, 1)
+        res, total_ms, ok, launches, solved = timed(B.QP_PREC_FP32, args.steps, args.warmup)
+    res64, total64, ok64, _, solved64 = timed(B.QP_PREC_FP64, args.fp64_steps, 1)
 
-    solved = sum(ok) * world
     value = solved / (total_ms / 1e3)
-    value64 = sum(ok64) * world / (total64 / 1e3)
+    value64 = solved64 / (total64 / 1e3)
 
     # ---- roofline of the dominant kernel chain: one PCG iteration (a6-a10)
     o = opts(B.QP_PREC_FP32)
@@ -269,7 +278,8 @@ def run_ours(args):
         e2e_ok += int(abs(f - gold["f"]) / max(abs(gold["f"]), 1.0) <= 1e-6 and st == 0)
     h2d = 8 * (qp.n * qp.n + qp.m1 * qp.n + qp.m2 * qp.n + qp.n + qp.m1 + qp.m2)
     d2h = 8 * qp.n + 8
-    e2e = {"value": e2e_ok * world / (e2e_ms / 1e3), "unit": "QPs/s", "h2d_bytes_per_step": h2d,
+    e2e_ms, e2e_solved = reduce_over_ranks(e2e_ms, e2e_ok, dev)
+    e2e = {"value": e2e_solved / (e2e_ms / 1e3), "unit": "QPs/s", "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h}
 
     if rank == 0:

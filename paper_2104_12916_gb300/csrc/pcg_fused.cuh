@@ -104,6 +104,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* b, unsigned parity) {
         : "memory");
     return ok != 0;
 }
+// Non-blocking test of the completion of the phase of parity `parity` of `b`.
+__device__ __forceinline__ bool mbar_test(uint64_t* b, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
 // Bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16);
 // completion is counted in bytes on `bar`.
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
@@ -239,9 +251,11 @@ __device__ __forceinline__ void block_range(int rows, int cols, int CH, long lon
 }
 
 // Producer side of one phase: each lane copies the items whose slot it owns, in
-// increasing order.  `g0` is the ring sequence number of the phase's first item
-// (advanced by the item count).  Returns false (in every lane) once the
-// consumers have stopped or a wait gave up.
+// increasing order.  The lanes poll together (a non-blocking test of their
+// slot's empty barrier per round), so a lane whose slot is still in use never
+// holds up a lane whose slot is free.  `g0` is the ring sequence number of the
+// phase's first item (advanced by the item count).  Returns false (in every
+// lane) once the consumers have stopped or the phase took longer than kWaitNs.
 template <typename TM, int TRI>
 __device__ __forceinline__ bool produce_phase(const TM* __restrict__ M, int rows, int cols, long long ld,
                                               const Ring& R, long long& g0) {
@@ -252,30 +266,39 @@ __device__ __forceinline__ bool produce_phase(const TM* __restrict__ M, int rows
     block_range<TRI>(rows, cols, CH, b0, cnt);
     int c = 0, row = 0;
     long long base = 0;
-    bool ok = true;
-    int slot = (int)(g0 % R.S);
-    int fill = (int)(g0 / R.S);
-    for (long long i = 0; i < cnt; ++i, ++slot) {
-        if (slot == R.S) { slot = 0; ++fill; }
-        if ((slot & 31) != lane) continue;
-        if (*R.stop) { ok = false; break; }
-        item_at<TRI>(b0 + i, rows, nc, CH, c, base, row);
-        if (fill > 0) {
-            // the slot is free once its previous chunk has been consumed
-            const unsigned par = (unsigned)((fill - 1) & 1);
-            bool got = mbar_try_wait(&R.empty[slot], par);
-            if (!got) {
-                const unsigned long long t0 = gtimer();
-                while (!(got = mbar_try_wait(&R.empty[slot], par)))
-                    if (*R.stop || gtimer() - t0 > kWaitNs) break;
-            }
-            if (!got) { ok = false; break; }
+    // this lane's next item: the first i >= from whose slot it owns
+    auto next_owned = [&](long long from) {
+        long long j = from;
+        int sl = (int)((g0 + j) % R.S);
+        while (j < cnt && (sl & 31) != lane) {
+            ++j;
+            if (++sl == R.S) sl = 0;
         }
-        const long long e0 = (long long)c * CH;
-        const unsigned bytes = (unsigned)(min((long long)CH, ld - e0) * (long long)sizeof(TM));
-        R.last_fill[slot] = fill;
-        mbar_expect_tx(&R.full[slot], bytes);
-        bulk_g2s(R.buf + (size_t)slot * kSlotBytes, M + (long long)row * ld + e0, bytes, &R.full[slot]);
+        return j;
+    };
+    long long i = next_owned(0);
+    bool ok = true;
+    unsigned polls = 0;
+    const unsigned long long t0 = gtimer();
+    while (true) {
+        const bool has = ok && i < cnt;
+        if (!__any_sync(0xffffffffu, has)) break;
+        if (has) {
+            const long long g = g0 + i;
+            const int slot = (int)(g % R.S);
+            const int fill = (int)(g / R.S);
+            // the slot is free once its previous chunk has been consumed
+            if (fill == 0 || mbar_test(&R.empty[slot], (unsigned)((fill - 1) & 1))) {
+                item_at<TRI>(b0 + i, rows, nc, CH, c, base, row);
+                const long long e0 = (long long)c * CH;
+                const unsigned bytes = (unsigned)(min((long long)CH, ld - e0) * (long long)sizeof(TM));
+                R.last_fill[slot] = fill;
+                mbar_expect_tx(&R.full[slot], bytes);
+                bulk_g2s(R.buf + (size_t)slot * kSlotBytes, M + (long long)row * ld + e0, bytes, &R.full[slot]);
+                i = next_owned(i + 1);
+            }
+        }
+        if ((++polls & 63) == 0 && (*R.stop || gtimer() - t0 > kWaitNs)) ok = false;
     }
     g0 += cnt;
     return __all_sync(0xffffffffu, ok);
