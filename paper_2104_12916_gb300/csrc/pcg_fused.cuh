@@ -402,6 +402,29 @@ __device__ __forceinline__ void stage_sum(TX* xs, const TM* part, int pld, int c
     }
 }
 
+// stage_sum with an operand loaded before the partials: pre(j) is issued for the
+// four rows together with their partial loads, and f(j, sum, pre(j)) makes the
+// staged value, so a loop-invariant vector costs no extra round trip.
+template <typename TX, typename TM, int TRI, class P, class F>
+__device__ __forceinline__ void stage_sum_pre(TX* xs, const TM* part, int pld, int cols, int len, int pad, P pre,
+                                              F f) {
+    using AT = typename Acc<TM>::type;
+    for (int j0 = threadIdx.x; j0 < pad; j0 += 4 * kFusedThreads) {
+        int j[4];
+        AT sm[4];
+        decltype(pre(0)) pv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            j[u] = j0 + u * kFusedThreads;
+            pv[u] = (j[u] < len) ? pre(j[u]) : decltype(pre(0))(0);
+        }
+        sum_chunks4<TM, TRI, AT>(part, pld, cols, j, len, sm);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (j[u] < pad) xs[j[u]] = (j[u] < len) ? f(j[u], sm[u], pv[u]) : TX(0);
+    }
+}
+
 // Consumer-wide fixed-order sum, result broadcast to every consumer thread.
 template <typename AT>
 __device__ __forceinline__ AT block_allsum(AT v, AT* sh) {
@@ -617,17 +640,21 @@ __global__ void __launch_bounds__(kFusedBlock, 1) pcg_fused_kernel(const FusedAr
         mark(it, 6);
 
         // ---- P5 (a10): q = D p + C y (cached), alpha = r'z / p'q, x += alpha p, r -= alpha q
-        stage_sum<TO, TO, TRI_NONE>(qc, a.PQ, a.ldQ, n, m2, m2,
-                                    [&](int j, AT v) { return (TO)fma((AT)__ldg(a.D + j), (AT)pcs[j], v); });
-        csync();
+        // (p'q is summed while q is staged: each thread takes its rows in increasing order)
         AT pq = AT(0);
-        for (int j = tid; j < m2; j += kFusedThreads) pq = fma((AT)pcs[j], (AT)qc[j], pq);
+        stage_sum_pre<TO, TO, TRI_NONE>(qc, a.PQ, a.ldQ, n, m2, m2, [&](int j) { return __ldg(a.D + j); },
+                                        [&](int j, AT v, TO dj) {
+                                            const TO q = (TO)fma((AT)dj, (AT)pcs[j], v);
+                                            pq = fma((AT)pcs[j], (AT)q, pq);
+                                            return q;
+                                        });
         pq = block_allsum(pq, sh);
         // breakdown (p'q <= 0 or not finite): stop with the last iterate untouched
         if (!(pq > AT(0)) || !isfinite(pq)) { done = 3; break; }
         const AT alpha = rz / pq;
         const TO al = (TO)alpha;
         AT rrp = AT(0), rzp = AT(0);
+#pragma unroll 4
         for (int j = tid; j < padO_m2; j += kFusedThreads) {
             if (j >= m2) {
                 if (PC == PC_H_K) { if (j < padP_m2) xp[j] = TP(0); } else xs[j] = TO(0);
@@ -673,11 +700,14 @@ __global__ void __launch_bounds__(kFusedBlock, 1) pcg_fused_kernel(const FusedAr
             if (!gsync()) { leave(); return; }
             mark(it - 1, 9);
             // z into the q cache (q is no longer needed), then r'z
-            stage_sum<TO, TP, TRI_UPPER>(qc, a.PZ, a.ldZ, m2, m2, m2,
-                                         [&](int j, typename Acc<TP>::type v) { return (TO)((AT)__ldg(a.sg + j) * (AT)v); });
-            csync();
+            // (r'z is summed while z is staged, rows in increasing order per thread)
             rzp = AT(0);
-            for (int j = tid; j < m2; j += kFusedThreads) rzp = fma((AT)rc[j], (AT)qc[j], rzp);
+            stage_sum_pre<TO, TP, TRI_UPPER>(qc, a.PZ, a.ldZ, m2, m2, m2, [&](int j) { return __ldg(a.sg + j); },
+                                             [&](int j, typename Acc<TP>::type v, TP sj) {
+                                                 const TO z = (TO)((AT)sj * (AT)v);
+                                                 rzp = fma((AT)rc[j], (AT)z, rzp);
+                                                 return z;
+                                             });
             rz_new = block_allsum(rzp, sh);
         } else {
             rz_new = block_allsum(rzp, sh);
@@ -686,6 +716,7 @@ __global__ void __launch_bounds__(kFusedBlock, 1) pcg_fused_kernel(const FusedAr
         const AT beta = rz_new / rz;
         rz = rz_new;
         const TO be = (TO)beta;
+#pragma unroll 4
         for (int j = tid; j < padO_m2; j += kFusedThreads) {
             TO v = TO(0);
             if (j < m2) {
