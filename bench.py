@@ -43,12 +43,15 @@ def parse():
     ap.add_argument("--profile-pcg", type=int, default=0, metavar="ITERS",
                     help="only factor the QP and run ITERS PCG iterations (a short run for ncu)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"], help="precision of --profile-pcg")
-    ap.add_argument("--workload", default="single", choices=["single", "serving"],
-                    help="serving: a Poisson stream of the served workload's QPs through qp_server_*")
+    ap.add_argument("--workload", default="single", choices=["single", "batch", "serving"],
+                    help="batch: the 512 batched QPs through qp_batch_solve; "
+                         "serving: a Poisson stream of the served workload's QPs through qp_server_*")
+    ap.add_argument("--batch", type=int, default=512, help="batch: number of QPs")
+    ap.add_argument("--concurrency", type=int, default=16, help="batch: QPs in flight")
     ap.add_argument("--requests", type=int, default=64, help="serving: number of requests")
     ap.add_argument("--rate", type=float, default=50.0, help="serving: arrival rate (requests/s)")
     ap.add_argument("--budget-gb", type=float, default=150.0, help="serving: HBM admission budget")
-    ap.add_argument("--slots", type=int, default=16, help="serving: QPs in flight at most")
+    ap.add_argument("--slots", type=int, default=64, help="serving: QPs in flight at most")
     ap.add_argument("--max-n", type=int, default=4096, help="serving: skip requests with n above this")
     return ap.parse_args()
 
@@ -369,6 +372,74 @@ def run_profile(args):
     B.qp_destroy(h)
 
 
+BATCH_WORKLOAD = ("512 dense QPs, n uniform [64,512], m_eq uniform [0.1n,0.5n], m_in uniform [n,3n], "
+                  "Lambda log-uniform [1e-2,1e2], seeds 1e6+i")
+
+
+def run_batch(args):
+    """The batched workload through qp_batch_solve: every QP created from host
+    buffers, solved with many in flight (each QP's persistent PCG kernel on 8-16
+    blocks launched as one cluster, host waits yielding), the solution read back.  One step = the whole batch,
+    timed on the host clock around qp_batch_solve (inputs already on the device);
+    e2e includes the creation (H2D) and the solution copies.  QPs with n <= 160
+    are checked against the FP64 oracle."""
+    world, rank, local = dist_env()
+    if rank != 0:
+        return
+    from paper_2104_12916_gb300 import binding as B, build
+    build.build()
+    B.load()
+    qps = [qpgen.batch_qp(i) for i in range(args.batch)]
+    out = {}
+    for prec in (B.QP_PREC_FP32, B.QP_PREC_FP64):
+        o = B.qp_opts_default()
+        o.precision, o.blocking_wait = prec, 1
+        l0 = B.qp_kernel_launches()
+        with ClockSampler(local) as clk:
+            t0 = time.perf_counter()
+            hs = [B.QP.from_qpgen(q, o) for q in qps]
+            t1 = time.perf_counter()
+            st, res = B.qp_batch_solve([h.h for h in hs], max_concurrent=args.concurrency)
+            t2 = time.perf_counter()
+            xs = []
+            for q, h in zip(qps, hs):
+                x = np.zeros(q.n)
+                B.qp_get_solution(h.h, x)
+                xs.append(x)
+            t3 = time.perf_counter()
+        for h in hs:
+            h.close()
+        ok = [r["status"] == 0 for r in res]
+        out[prec] = dict(res=res, ok=ok, solve_s=t2 - t1, e2e_s=t3 - t0, launches=B.qp_kernel_launches() - l0,
+                         clocks=clk.summary())
+    from oracle import ipm
+    errs = []
+    r32 = out[B.QP_PREC_FP32]["res"]
+    for i, q in enumerate(qps):
+        if q.n <= 160:
+            ref = ipm.solve_qp(q, variant="kkt3")
+            errs.append(abs(r32[i]["obj"] - ref.f) / max(abs(ref.f), 1.0))
+    m = out[B.QP_PREC_FP32]
+    m64 = out[B.QP_PREC_FP64]
+    h2d = sum(8 * (q.n * q.n + q.m1 * q.n + q.m2 * q.n + q.n + q.m1 + q.m2) for q in qps)
+    line = {"metric": "QPs solved/s on the 512-QP batch (mixed precision; FP64 path alongside)",
+            "value": round(sum(m["ok"]) / m["solve_s"], 3), "unit": "QPs/s", "n_gpus": 1, "steps": 1, "warmup": 0,
+            "ms_per_step": round(m["solve_s"] * 1e3, 1), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": BATCH_WORKLOAD, "qps": len(qps), "in_flight": args.concurrency,
+                       "precision": "mixed (FP32 operator and P_H, FP64 refinement)"},
+            "solved": f"{sum(m['ok'])}/{len(qps)}",
+            "fp64": {"value": round(sum(m64["ok"]) / m64["solve_s"], 3), "unit": "QPs/s",
+                     "solved": f"{sum(m64['ok'])}/{len(qps)}"},
+            "oracle_checked": len(errs), "oracle_max_rel_err": max(errs) if errs else None,
+            "latency_ms": {"p50": round(float(np.percentile([r["solve_ms"] for r in m["res"]], 50)), 1),
+                           "p99": round(float(np.percentile([r["solve_ms"] for r in m["res"]], 99)), 1)},
+            "e2e": {"value": round(sum(m["ok"]) / m["e2e_s"], 3), "unit": "QPs/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": sum(8 * q.n for q in qps)},
+            "gpu_launches": int(m["launches"]), "clocks": m["clocks"]}
+    print(json.dumps(line), flush=True)
+
+
 SERVING_WORKLOAD = ("served stream: n log-uniform [64,4096], m_eq = n U(0.05,0.9), m_in = n U(1,3), "
                     "C CSR 8 nnz/row, Lambda log-uniform [1e-2,1e2], Poisson arrivals")
 
@@ -390,6 +461,7 @@ def run_serving(args):
     qps = [qpgen.serving_qp(i) for i in idx]
     arrive = qpgen.arrival_times(len(qps), args.rate)
     o = B.qp_opts_default()
+    o.blocking_wait = 1
     srv = B.Server(budget_bytes=int(args.budget_gb * 1e9), max_slots=args.slots, opts=o)
     l0 = B.qp_kernel_launches()
     results = {}
@@ -444,6 +516,8 @@ if __name__ == "__main__":
     a = parse()
     if a.workload == "serving" and a.impl == "ours":
         run_serving(a)
+    elif a.workload == "batch" and a.impl == "ours":
+        run_batch(a)
     elif a.profile_pcg:
         run_profile(a)
     elif a.impl == "reference":

@@ -61,9 +61,10 @@ enum qp_status {
 
 enum qp_precision {
     QP_PREC_FP64 = 0,     /* factor, C copies and PCG all in FP64 */
-    QP_PREC_FP32 = 1      /* mixed: P_H factor in FP32; C copies, K0 factor and PCG in FP32 until
-                             FP64 refinement contracts by less than 4x per sweep, then in FP64
-                             (a second, FP64 factor of K0); FP64 residuals, refinement, step logic */
+    QP_PREC_FP32 = 1      /* mixed: C copies, K0 factor and PCG in FP32 until FP64 refinement
+                             contracts by less than 4x per sweep, then in FP64 (a second, FP64
+                             factor of K0); P_H in FP32 until its factorization needs a shift, then
+                             in FP64; FP64 residuals, refinement, step logic */
 };
 
 enum qp_precond {
@@ -103,6 +104,13 @@ typedef struct {
                              < 0: per-phase kernels in CUDA graphs of |value| iterations */
     int mixed_fallback;   /* QP_PREC_FP32 only: 1 (default) lets a QP move its operator and P_H to
                              FP64 when FP32 stops sufficing; 0 keeps FP32 (shifting P_H as needed) */
+    int pcg_blocks;       /* blocks of the persistent PCG kernel: 0 (default) = about one per 512 KB
+                             streamed per iteration (8 to 16 for a small QP, launched as one
+                             thread-block cluster; up to one per SM); k > 0 = at most k (with 1 the
+                             grid barriers become block barriers).  Results do not depend on it:
+                             every reduction has a fixed order independent of the grid. */
+    int blocking_wait;    /* 1: host waits on the solver's stream yield the CPU instead of spinning
+                             (many QPs in flight on more host threads than cores); default 0 */
     void *stream;         /* cudaStream_t, or NULL for a library-created stream */
 } qp_opts;
 

@@ -37,6 +37,7 @@ class qp_opts(ct.Structure):
         ("max_ipm", ct.c_int), ("max_pcg", ct.c_int), ("refine_max", ct.c_int),
         ("pcg_tol", ct.c_double), ("refine_tol", ct.c_double), ("tol_feas", ct.c_double),
         ("tol_mu", ct.c_double), ("pcg_check_every", ct.c_int), ("mixed_fallback", ct.c_int),
+        ("pcg_blocks", ct.c_int), ("blocking_wait", ct.c_int),
         ("stream", ct.c_void_p),
     ]
 

@@ -189,7 +189,7 @@ public:
     double* h_scal = nullptr;  // pinned
     int* d_info = nullptr;
     int* h_info = nullptr;     // pinned
-    cudaEvent_t ev0, ev1, evA, evB;
+    cudaEvent_t ev0, ev1, evA, evB, evW;
     int cap_rows = 0;
     int last_pcg_done = 0;
     double last_pcg_rel = 0.0;
@@ -228,10 +228,13 @@ public:
             own_stream = true;
         }
         arena.stream = s;
-        PCG_CK(cudaEventCreate(&ev0));
-        PCG_CK(cudaEventCreate(&ev1));
-        PCG_CK(cudaEventCreate(&evA));
-        PCG_CK(cudaEventCreate(&evB));
+        // blocking_wait: host waits yield the CPU (many QPs in flight, more host threads than cores)
+        const unsigned evf = opt.blocking_wait ? cudaEventBlockingSync : cudaEventDefault;
+        PCG_CK(cudaEventCreateWithFlags(&ev0, evf));
+        PCG_CK(cudaEventCreateWithFlags(&ev1, evf));
+        PCG_CK(cudaEventCreateWithFlags(&evA, evf));
+        PCG_CK(cudaEventCreateWithFlags(&evB, evf));
+        PCG_CK(cudaEventCreateWithFlags(&evW, evf | cudaEventDisableTiming));
         cap_rows = std::max(std::max(n, m2), std::max(m1, 512)) + 64;   // >= every partials grid
         const char* v = std::getenv("PCGIPM_VERBOSE");
         verbose = v && v[0] == '1';
@@ -256,6 +259,7 @@ public:
         cudaEventDestroy(ev1);
         cudaEventDestroy(evA);
         cudaEventDestroy(evB);
+        cudaEventDestroy(evW);
         arena.release();
         cudaStreamSynchronize(s);
         if (own_stream) cudaStreamDestroy(s);
@@ -308,8 +312,18 @@ public:
         return b;
     }
 
+    // Wait for the solver stream (spinning, or yielding with blocking_wait).
+    void wait_stream() {
+        if (opt.blocking_wait) {
+            PCG_CK(cudaEventRecord(evW, s));
+            PCG_CK(cudaEventSynchronize(evW));
+        } else {
+            PCG_CK(cudaStreamSynchronize(s));
+        }
+    }
+
     void sync_check() {
-        PCG_CK(cudaStreamSynchronize(s));
+        wait_stream();
         PCG_CK(cudaGetLastError());
     }
 
@@ -339,7 +353,7 @@ public:
                 last = csr->rowptr[m2];
             } else {
                 PCG_CK(cudaMemcpyAsync(&last, csr->rowptr + m2, sizeof(int), cudaMemcpyDeviceToHost, s));
-                PCG_CK(cudaStreamSynchronize(s));
+                wait_stream();
             }
             if (last < 0) throw QpError{QP_EINVAL};
             const long long nnz = last;
@@ -531,7 +545,7 @@ public:
         if (Aw) cudaFreeAsync(Aw, s);
         if (G) cudaFreeAsync(G, s);
         if (S) cudaFreeAsync(S, s);
-        PCG_CK(cudaStreamSynchronize(s));
+        wait_stream();
         PCG_CK(cudaGetLastError());
         if (h_info[0] != 0) throw QpError{QP_ENOTCONVEX};
         if (h_info[2] != 0) throw QpError{QP_ESINGULAR};
@@ -599,7 +613,7 @@ public:
         h.C = P.Tm.p; h.ldc = P.Tm.ld; h.alpha = TP(1); h.beta = TP(0); h.lower_out = 1;
         gemm<TP>(h, s);
         cudaFreeAsync(Bp, s);
-        PCG_CK(cudaStreamSynchronize(s));
+        wait_stream();
         PCG_CK(cudaGetLastError());
         P.t_kind = kind;
     }
@@ -851,7 +865,7 @@ public:
         if (phase_times && hst[0].iter >= 4) {
             unsigned long long t[4 * 32];
             PCG_CK(cudaMemcpyAsync(t, tstamp, sizeof(t), cudaMemcpyDeviceToHost, s));
-            PCG_CK(cudaStreamSynchronize(s));
+            wait_stream();
             std::fprintf(stderr, "phase marks (us from iteration start):");
             for (int i = 1; i < 4; ++i) {
                 std::fprintf(stderr, "\n  it %d:", i);
@@ -910,8 +924,10 @@ public:
     int fused_grid(int sms) const {
         const double by = bytes_per_iter(resolve_pc(opt.precond, n, m1));
         const int want = (int)std::ceil(by / (512.0 * 1024.0));
-        if (want <= 2 * kMaxClusterBlocks) return std::min(sms, std::max(8, std::min(want, kMaxClusterBlocks)));
-        return std::min(sms, want);
+        int g = (want <= 2 * kMaxClusterBlocks) ? std::min(sms, std::max(8, std::min(want, kMaxClusterBlocks)))
+                                                : std::min(sms, want);
+        if (opt.pcg_blocks > 0) g = std::min(g, opt.pcg_blocks);
+        return g;
     }
 
     // Runs PCG from the current pcg_init state until done; the final state ends in
@@ -942,9 +958,9 @@ public:
             }
             PCG_CK(cudaEventSynchronize(cur == 0 ? ev0 : ev1));
             if (hst[cur].done || !second) {
-                PCG_CK(cudaStreamSynchronize(s));
+                wait_stream();
                 PCG_CK(cudaMemcpyAsync(&hst[0], st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
-                PCG_CK(cudaStreamSynchronize(s));
+                wait_stream();
                 break;
             }
             cur = 1 - cur;
@@ -977,7 +993,10 @@ public:
     // Mixed precision: once the FP32 Cholesky of P~ needs a diagonal shift (P~ has
     // eigenvalues below FP32 resolution: with m2 > n, the directions in null(C')
     // where D_i << T_ii), the QP moves its preconditioner and its operator to FP64
-    // for the remaining IPM iterations.
+    // for the remaining IPM iterations.  (Applying the FP64 factor rounded to FP32
+    // instead keeps the preconditioner SPD, but after the switch the inner solves
+    // go to 1e-10 and a preconditioner applied at FP32 accuracy slows CG there:
+    // 53% more PCG iterations on the n=2000 workload.)
     void set_D(const double* Dd, int pc) {
         if (!pc64) {
             const double shift = set_D_pc<float>(Dd, pc);
@@ -1193,7 +1212,7 @@ public:
         job.njobs = 3;
         reduce_jobs_kernel<<<1, kVecThreads, 0, s>>>(job, d_scal);
         PCG_CK(cudaMemcpyAsync(h_scal, d_scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
-        PCG_CK(cudaStreamSynchronize(s));
+        wait_stream();
         return h_scal[0] + (m1 ? h_scal[1] : 0.0) + h_scal[2];
     }
 
@@ -1438,7 +1457,7 @@ public:
         if (lo && m1) PCG_CK(cudaMemcpyAsync(lo, lam, (size_t)m1 * 8, kd, s));
         if (no) PCG_CK(cudaMemcpyAsync(no, nu, (size_t)m2 * 8, kd, s));
         if (so) PCG_CK(cudaMemcpyAsync(so, sl, (size_t)m2 * 8, kd, s));
-        PCG_CK(cudaStreamSynchronize(s));
+        wait_stream();
     }
 };
 

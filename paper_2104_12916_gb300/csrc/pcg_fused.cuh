@@ -170,6 +170,15 @@ __device__ __forceinline__ bool grid_sync(GridBar* b, unsigned nblocks, unsigned
                                           int* s_flag) {
     csync();
     target += nblocks;
+    if (nblocks == 1) {   // a one-block grid: the block barrier above is the whole barrier
+        if (threadIdx.x == 0) {
+            const int e = *((volatile const int*)err);
+            if (e) atomicExch(&b->err, 2);
+            *s_flag = e;
+        }
+        csync();
+        return *s_flag == 0;
+    }
     if (threadIdx.x == 0) {
         if (*((volatile const int*)err)) atomicExch(&b->err, 2);
         __threadfence();
@@ -207,10 +216,10 @@ __device__ __forceinline__ void chunk_rows(int c, int CH, int rows, int& r0, int
 }
 
 template <int TRI>
-__device__ __forceinline__ long long chunk_items(int rows, int cols, int CH) {
+__device__ __forceinline__ int chunk_items(int rows, int cols, int CH) {
     const int nc = (cols + CH - 1) / CH;
-    if (TRI == TRI_NONE) return (long long)rows * nc;
-    long long t = 0;
+    if (TRI == TRI_NONE) return rows * nc;
+    int t = 0;
     for (int c = 0; c < nc; ++c) {
         int r0, r1;
         chunk_rows<TRI>(c, CH, rows, r0, r1);
@@ -219,64 +228,87 @@ __device__ __forceinline__ long long chunk_items(int rows, int cols, int CH) {
     return t;
 }
 
-// Item index -> (row, chunk).  `c`/`base` carry the last chunk column found so a
-// caller walking increasing item indices moves forward through the columns.
-template <int TRI>
-__device__ __forceinline__ void item_at(long long it, int rows, int nc, int CH, int& c, long long& base,
-                                        int& row) {
-    if constexpr (TRI == TRI_NONE) {
-        c = (int)(it / rows);
-        row = (int)(it - (long long)c * rows);
-    } else {
-        while (true) {
-            int r0, r1;
-            chunk_rows<TRI>(c, CH, rows, r0, r1);
-            if (it < base + (r1 - r0) || c == nc - 1) {
-                row = r0 + (int)(it - base);
-                return;
-            }
-            base += r1 - r0;
-            ++c;
-        }
-    }
-}
-
 // This block's contiguous item range [b0, b0 + cnt) of a phase.
 template <int TRI>
-__device__ __forceinline__ void block_range(int rows, int cols, int CH, long long& b0, long long& cnt) {
-    const long long nitems = chunk_items<TRI>(rows, cols, CH);
-    const long long per = (nitems + gridDim.x - 1) / gridDim.x;
-    b0 = (long long)blockIdx.x * per;
-    cnt = max(0LL, min(nitems, b0 + per) - b0);
+__device__ __forceinline__ void block_range(int rows, int cols, int CH, int& b0, int& cnt) {
+    const int nitems = chunk_items<TRI>(rows, cols, CH);
+    const int per = (nitems + (int)gridDim.x - 1) / (int)gridDim.x;
+    b0 = (int)blockIdx.x * per;
+    cnt = max(0, min(nitems, b0 + per) - b0);
 }
 
-// Producer side of one phase: each lane copies the items whose slot it owns, in
-// increasing order.  The lanes poll together (a non-blocking test of their
-// slot's empty barrier per round), so a lane whose slot is still in use never
-// holds up a lane whose slot is free.  `g0` is the ring sequence number of the
-// phase's first item (advanced by the item count).  Returns false (in every
-// lane) once the consumers have stopped or the phase took longer than kWaitNs.
+// (row, chunk column) of an item, walked forward from a starting item by
+// non-negative steps: one division when it starts, additions after.
+template <int TRI>
+struct ItemWalk {
+    int rows, nc, CH;
+    int it = 0, c = 0, base = 0, r0 = 0, r1 = 0, row = 0;
+    __device__ __forceinline__ ItemWalk(int rows_, int nc_, int CH_, int first) : rows(rows_), nc(nc_), CH(CH_) {
+        if constexpr (TRI == TRI_NONE) {
+            it = first;
+            c = first / rows;
+            row = first - c * rows;
+        } else {
+            chunk_rows<TRI>(0, CH, rows, r0, r1);
+            step(first);
+        }
+    }
+    __device__ __forceinline__ void step(int d) {
+        it += d;
+        if constexpr (TRI == TRI_NONE) {
+            row += d;
+            while (row >= rows) {
+                row -= rows;
+                ++c;
+            }
+        } else {
+            while (it >= base + (r1 - r0) && c < nc - 1) {
+                base += r1 - r0;
+                ++c;
+                chunk_rows<TRI>(c, CH, rows, r0, r1);
+            }
+            row = r0 + (it - base);
+        }
+    }
+};
+
+// Ring position of an item: its slot and fill number (sequence number fill * S + slot).
+struct RingPos {
+    int slot = 0, fill = 0;
+    __device__ __forceinline__ void advance(int d, int S) {   // any d >= 0
+        slot += d;
+        if (slot >= S) {
+            fill += slot / S;
+            slot %= S;
+        }
+    }
+};
+
+// Producer side of one phase: each lane copies the items whose slot it owns
+// (slots lane and lane + 32), in increasing order.  The lanes poll together (a
+// non-blocking test of their slot's empty barrier per round), so a lane whose
+// slot is still in use never holds up a lane whose slot is free.  `pos` is the
+// ring position of the phase's first item (advanced past the phase).  Returns
+// false (in every lane) once the consumers have stopped or the phase took
+// longer than kWaitNs.
 template <typename TM, int TRI>
 __device__ __forceinline__ bool produce_phase(const TM* __restrict__ M, int rows, int cols, long long ld,
-                                              const Ring& R, long long& g0) {
+                                              const Ring& R, RingPos& pos) {
     constexpr int CH = Chunk<TM>::n;
     const int lane = threadIdx.x & 31;
     const int nc = (cols + CH - 1) / CH;
-    long long b0, cnt;
+    const int S = R.S;
+    int b0, cnt;
     block_range<TRI>(rows, cols, CH, b0, cnt);
-    int c = 0, row = 0;
-    long long base = 0;
-    // this lane's next item: the first i >= from whose slot it owns
-    auto next_owned = [&](long long from) {
-        long long j = from;
-        int sl = (int)((g0 + j) % R.S);
-        while (j < cnt && (sl & 31) != lane) {
-            ++j;
-            if (++sl == R.S) sl = 0;
-        }
-        return j;
-    };
-    long long i = next_owned(0);
+    // owned slots, and the distance from one slot to another along the ring
+    const int o1 = lane < S ? lane : -1, o2 = lane + 32 < S ? lane + 32 : -1;
+    auto dist = [&](int from, int to) { return to >= from ? to - from : to + S - from; };
+    int i = cnt;
+    if (o1 >= 0) i = dist(pos.slot, o1);
+    if (o2 >= 0) i = min(i, dist(pos.slot, o2));
+    RingPos me = pos;
+    me.advance(i < cnt ? i : 0, S);
+    ItemWalk<TRI> w(rows, nc, CH, b0 + (i < cnt ? i : 0));
     bool ok = true;
     unsigned polls = 0;
     const unsigned long long t0 = gtimer();
@@ -284,31 +316,35 @@ __device__ __forceinline__ bool produce_phase(const TM* __restrict__ M, int rows
         const bool has = ok && i < cnt;
         if (!__any_sync(0xffffffffu, has)) break;
         if (has) {
-            const long long g = g0 + i;
-            const int slot = (int)(g % R.S);
-            const int fill = (int)(g / R.S);
+            const int slot = me.slot, fill = me.fill;
             // the slot is free once its previous chunk has been consumed
             if (fill == 0 || mbar_test(&R.empty[slot], (unsigned)((fill - 1) & 1))) {
-                item_at<TRI>(b0 + i, rows, nc, CH, c, base, row);
-                const long long e0 = (long long)c * CH;
+                const long long e0 = (long long)w.c * CH;
                 const unsigned bytes = (unsigned)(min((long long)CH, ld - e0) * (long long)sizeof(TM));
                 R.last_fill[slot] = fill;
                 mbar_expect_tx(&R.full[slot], bytes);
-                bulk_g2s(R.buf + (size_t)slot * kSlotBytes, M + (long long)row * ld + e0, bytes, &R.full[slot]);
-                i = next_owned(i + 1);
+                bulk_g2s(R.buf + (size_t)slot * kSlotBytes, M + (long long)w.row * ld + e0, bytes, &R.full[slot]);
+                // next owned slot: the lane's other slot, else the same slot one lap later
+                const int other = (slot == o1) ? o2 : o1;
+                const int d = (other >= 0) ? dist(slot, other) : S;
+                i += d;
+                if (i < cnt) {
+                    me.advance(d, S);
+                    w.step(d);
+                }
             }
         }
         if ((++polls & 63) == 0 && (*R.stop || gtimer() - t0 > kWaitNs)) ok = false;
     }
-    g0 += cnt;
+    pos.advance(cnt, S);
     return __all_sync(0xffffffffu, ok);
 }
 
 // Consumer side of one phase: part[c * pld + row] = chunk c of row `row` of M . xs
 // (chunk-major, so that the next phase's per-row sums load coalesced).  Warp w
-// takes the items whose ring sequence number g is w modulo kFusedWarps.
+// takes the items whose slot is w modulo kFusedWarps (S is a multiple of it).
 template <typename TM, int TRI>
-__device__ __forceinline__ void gemv_ring(const Ring& R, long long& g0, int rows, int cols, long long ld,
+__device__ __forceinline__ void gemv_ring(const Ring& R, RingPos& pos, int rows, int cols, long long ld,
                                           const TM* __restrict__ xs, TM* __restrict__ part, int pld,
                                           int* err) {
     using VT = Vec16<TM>;
@@ -318,33 +354,39 @@ __device__ __forceinline__ void gemv_ring(const Ring& R, long long& g0, int rows
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int nc = (cols + CH - 1) / CH;
-    long long b0, cnt;
+    const int S = R.S;
+    int b0, cnt;
     block_range<TRI>(rows, cols, CH, b0, cnt);
     const V* xv = reinterpret_cast<const V*>(xs);
-    int c = 0, row = 0;
-    long long base = 0;
-    const long long first = (long long)((warp - (int)(g0 % kFusedWarps) + kFusedWarps) % kFusedWarps);
-    for (long long i = first; i < cnt; i += kFusedWarps) {
-        item_at<TRI>(b0 + i, rows, nc, CH, c, base, row);
-        const int vbase = c * (CH / VN);
-        const long long g = g0 + i;
-        const int slot = (int)(g % R.S);
-        if (!mbar_wait(&R.full[slot], (unsigned)((g / R.S) & 1))) *err = 1;
-        const V* sv = reinterpret_cast<const V*>(R.buf + (size_t)slot * kSlotBytes);
-        const int vend = (int)(ld / VN) - vbase;   // vectors of this row from the chunk start
-        TM acc = TM(0);
+    const int first = (warp - pos.slot % kFusedWarps + kFusedWarps) % kFusedWarps;
+    if (first < cnt) {
+        RingPos me = pos;
+        me.advance(first, S);
+        ItemWalk<TRI> w(rows, nc, CH, b0 + first);
+        for (int i = first; i < cnt; i += kFusedWarps) {
+            const int vbase = w.c * (CH / VN);
+            const int slot = me.slot;
+            if (!mbar_wait(&R.full[slot], (unsigned)(me.fill & 1))) *err = 1;
+            const V* sv = reinterpret_cast<const V*>(R.buf + (size_t)slot * kSlotBytes);
+            const int vend = (int)(ld / VN) - vbase;   // vectors of this row from the chunk start
+            TM acc = TM(0);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int v = lane + 32 * k;
-            const V m = (v < vend) ? sv[v] : V{};
-            acc = VT::dot(m, xv[vbase + v], acc);
+            for (int k = 0; k < 8; ++k) {
+                const int v = lane + 32 * k;
+                const V m = (v < vend) ? sv[v] : V{};
+                acc = VT::dot(m, xv[vbase + v], acc);
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&R.empty[slot]);
+            acc = warp_sum(acc);
+            if (lane == 0) part[(long long)w.c * pld + w.row] = acc;
+            if (i + kFusedWarps < cnt) {
+                me.advance(kFusedWarps, S);
+                w.step(kFusedWarps);
+            }
         }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&R.empty[slot]);
-        acc = warp_sum(acc);
-        if (lane == 0) part[(long long)c * pld + row] = acc;
     }
-    g0 += cnt;
+    pos.advance(cnt, S);
 }
 
 // Chunk sums of four rows j[0..3] at once (rows >= len give 0): for each row the
@@ -485,7 +527,7 @@ inline size_t fused_smem_bytes(size_t ring_off, int slots) {
 template <typename TO, typename TP, int PC>
 __device__ void pcg_producer(const FusedArgs<TO, TP>& a, const Ring& R) {
     const int n = a.n, m1 = a.m1, m2 = a.m2;
-    long long g = 0;
+    RingPos g;
     while (!*R.stop) {   // (a block may own no chunk of any phase: it polls the stop flag here)
         if (!produce_phase<TO, TRI_NONE>(a.CWT, n, m2, a.ldCWT, R, g)) break;
         if (!produce_phase<TO, TRI_LOWER>(a.WH, n, n, a.ldWH, R, g)) break;
@@ -567,7 +609,7 @@ __global__ void __launch_bounds__(kFusedBlock, 1) pcg_fused_kernel(const FusedAr
         if (stamp && it < 4) a.tstamp[it * 32 + ph] = gtimer();
     };
     unsigned target = 0;
-    long long g = 0;   // ring sequence number of the next chunk
+    RingPos g;   // ring position of the next chunk
     // every consumer exit passes here: the producer stops issuing and drains
     auto leave = [&]() {
         csync();

@@ -78,6 +78,8 @@ void qp_opts_default(qp_opts* o) {
     o->tol_mu = 1e-11;
     o->pcg_check_every = 8;
     o->mixed_fallback = 1;
+    o->pcg_blocks = 0;
+    o->blocking_wait = 0;
     o->stream = nullptr;
 }
 

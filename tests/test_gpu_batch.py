@@ -79,3 +79,37 @@ def test_auto_moves_from_pl_to_ph_when_pl_stops_converging(B, prec):
     assert abs(f - ref.f) / max(abs(ref.f), 1.0) <= 1e-9
     assert abs(its - ref.iters) <= 2
     h.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_one_block_grid_gives_identical_results(B, prec):
+    """pcg_blocks = 1 runs the persistent PCG kernel on a single block (block
+    barriers only): every reduction keeps its order, so the solution is
+    bit-identical to the default grid's; and a batch of such QPs with many in
+    flight (blocking host waits) matches too."""
+    qps = _mini_batch(6, seed0=900)
+    for q in qps[:2]:
+        xs = []
+        for blocks in (0, 1):
+            o = B.qp_opts_default()
+            o.precision, o.pcg_blocks = prec, blocks
+            h = B.QP.from_qpgen(q, o)
+            x = np.zeros(q.n)
+            B.qp_ipm_solve(h.h, x)
+            xs.append(x)
+            h.close()
+        assert np.array_equal(xs[0], xs[1]), q.name
+    o = B.qp_opts_default()
+    o.precision, o.pcg_blocks, o.blocking_wait = prec, 1, 1
+    handles = [B.QP.from_qpgen(q, o) for q in qps]
+    st, res = B.qp_batch_solve([h.h for h in handles], max_concurrent=len(qps))
+    assert st == B.QP_OK, res
+    for q, h in zip(qps, handles):
+        x = np.zeros(q.n)
+        B.qp_get_solution(h.h, x)
+        o2 = B.qp_opts_default()
+        o2.precision = prec
+        h2 = B.QP.from_qpgen(q, o2)
+        x2 = np.zeros(q.n)
+        B.qp_ipm_solve(h2.h, x2)
+        assert np.array_equal(x, x2), q.name
