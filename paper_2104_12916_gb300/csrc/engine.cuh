@@ -772,8 +772,21 @@ public:
 
     // The persistent cooperative PCG kernel: one launch runs the whole solve from
     // the pcg_init state (x = 0, r = rhs, p = z0); the final state ends in hst[0].
+    // Small QPs (a grid of at most kMaxClusterBlocks) run 256-thread blocks, two per
+    // SM; larger ones 512-thread blocks, one per SM.  The choice depends only on
+    // the QP's sizes, so a QP's results do not depend on what else runs.
     template <typename TO, typename TP, int PC>
     void launch_fused() {
+        int dev = 0, sms = 0;
+        PCG_CK(cudaGetDevice(&dev));
+        PCG_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        const int grid = fused_grid(sms);
+        if (grid <= kMaxClusterBlocks) launch_fused_nt<TO, TP, PC, kSmallBlock>(grid, sms);
+        else launch_fused_nt<TO, TP, PC, kBigBlock>(grid, sms);
+    }
+
+    template <typename TO, typename TP, int PC, int NT>
+    void launch_fused_nt(int grid, int sms) {
         Op<TO>& o = op<TO>();
         Pc<TP>& P = pcd<TP>();
         FusedArgs<TO, TP> fa{};
@@ -790,20 +803,17 @@ public:
         fa.ldV = P.ldV; fa.ldZ = P.ldV;
         fa.st = st; fa.bar = bar;
         fa.tstamp = phase_times ? tstamp : nullptr;
-        auto kern = pcg_fused_kernel<TO, TP, PC>;
+        auto kern = pcg_fused_kernel<TO, TP, PC, NT>;
         const size_t xsb = fused_xs_bytes<TO, TP>();
         fa.xs_bytes = xsb;
         fa.ring_off = fused_ring_offset<TO>(xsb, m2);
-        int dev = 0, sms = 0, per_sm = 0;
-        PCG_CK(cudaGetDevice(&dev));
-        PCG_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        const int grid = fused_grid(sms);
+        int per_sm = 0;
         // A QP whose grid covers most of the GPU takes the deepest ring that fits; a
         // small one (batched with others) a shallow ring, so that the blocks of several
         // QPs share an SM.
-        fa.slots = fused_slots<TO, TP>();
-        if (2 * grid < sms) fa.slots = std::min(fa.slots, kSmallRingSlots);
-        if (fa.slots < kMinSlots) throw QpError{QP_ENOMEM};
+        fa.slots = fused_slots<TO, TP, NT>();
+        if (2 * grid < sms) fa.slots = std::min(fa.slots, Blk<NT>::small_slots);
+        if (fa.slots < Blk<NT>::warps) throw QpError{QP_ENOMEM};
         const size_t smem = fused_smem_bytes(fa.ring_off, fa.slots);
         // Kernel attributes are shared by every thread of the process: set them once
         // (the dynamic shared-memory limit to what fused_slots() sizes the ring for;
@@ -815,7 +825,7 @@ public:
             return e;
         }();
         PCG_CK(attr_ok);
-        PCG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kFusedBlock, smem));
+        PCG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
         if (per_sm < 1) throw QpError{QP_ENOMEM};
         PCG_CK(cudaMemsetAsync(bar, 0, sizeof(GridBar), s));
         // A grid of at most kMaxClusterBlocks blocks is launched as one thread-block
@@ -824,7 +834,7 @@ public:
         // time run side by side.  Larger grids use a cooperative launch.
         cudaLaunchConfig_t cfg{};
         cfg.gridDim = dim3(grid);
-        cfg.blockDim = dim3(kFusedBlock);
+        cfg.blockDim = dim3(NT);
         cfg.dynamicSmemBytes = smem;
         cfg.stream = s;
         cudaLaunchAttribute at[1];
@@ -849,7 +859,7 @@ public:
             PCG_CK(cudaLaunchKernelEx(&cfg, kern, fa));
         } else {
             void* args[] = {(void*)&fa};
-            PCG_CK(cudaLaunchCooperativeKernel((const void*)kern, grid, kFusedBlock, args, smem, s));
+            PCG_CK(cudaLaunchCooperativeKernel((const void*)kern, grid, NT, args, smem, s));
         }
     }
 
@@ -879,7 +889,7 @@ public:
 
     // Shared memory of the persistent kernel: one staged vector, three m2-vectors,
     // and a ring of 4 KB chunk slots as deep as the rest of the block's limit allows
-    // (at most kMaxSlots).  With fewer than kMinSlots slots the per-phase kernels
+    // (at most three slots per consumer warp).  With fewer slots than consumer warps the per-phase kernels
     // are used instead.
     static size_t fused_smem_limit() {
         static const size_t lim = []() {
@@ -901,18 +911,22 @@ public:
         const size_t xsb = std::max(elems * sizeof(TO), padto(m2, CP) * sizeof(TP));
         return (xsb + 15) / 16 * 16;
     }
-    template <typename TO, typename TP>
+    template <typename TO, typename TP, int NT>
     int fused_slots() const {
         const size_t off = fused_ring_offset<TO>(fused_xs_bytes<TO, TP>(), m2);
         const size_t lim = fused_smem_limit();
         const size_t per = kSlotBytes + 2 * sizeof(uint64_t) + sizeof(int);
         if (off + 16 + per > lim) return 0;
-        const int sl = (int)std::min<size_t>(kMaxSlots, (lim - off - 16) / per);
-        return sl / kFusedWarps * kFusedWarps;   // the ring protocol wants a multiple of the consumer warps
+        const int sl = (int)std::min<size_t>(Blk<NT>::max_slots, (lim - off - 16) / per);
+        return sl / Blk<NT>::warps * Blk<NT>::warps;   // the ring protocol wants a multiple of the consumer warps
     }
     template <typename TO, typename TP>
     bool fused_fits() const {
-        return fused_slots<TO, TP>() >= kMinSlots;
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (fused_grid(sms) <= kMaxClusterBlocks) return fused_slots<TO, TP, kSmallBlock>() >= Blk<kSmallBlock>::warps;
+        return fused_slots<TO, TP, kBigBlock>() >= Blk<kBigBlock>::warps;
     }
 
     bool use_fused() const { return opt.pcg_check_every >= 0; }

@@ -42,13 +42,17 @@
 
 namespace pcgipm {
 
-constexpr int kFusedBlock = 512;                    // threads per block
-constexpr int kFusedThreads = kFusedBlock - 32;     // consumer threads (the last warp produces)
-constexpr int kFusedWarps = kFusedThreads / 32;
+// Block sizes: 512 threads for a QP that spreads over the GPU (one block per SM),
+// 256 for a small QP (two blocks per SM, so that blocks of different QPs hide one
+// another's barrier waits).  The last warp of a block is the producer.
+constexpr int kBigBlock = 512, kSmallBlock = 256;
+template <int NT> struct Blk {
+    static constexpr int threads = NT - 32;            // consumer threads
+    static constexpr int warps = threads / 32;         // consumer warps
+    static constexpr int max_slots = 3 * warps;        // ring depths are multiples of `warps`
+    static constexpr int small_slots = 2 * warps;      // ring of a QP that shares the GPU
+};
 constexpr int kSlotBytes = 4096;
-constexpr int kMaxSlots = 3 * kFusedWarps;       // ring depths are multiples of kFusedWarps
-constexpr int kMinSlots = kFusedWarps;
-constexpr int kSmallRingSlots = kFusedWarps;      // ring of a QP that shares the GPU
 constexpr int kMaxClusterBlocks = 16;             // grids up to this size launch as one cluster
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s bound on any wait
 
@@ -144,8 +148,8 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity) {
 //  - producer lane s % 32 issues every fill of slot s; before fill f it waits
 //    for the consumption of fill f - 1, and it had waited for that of f - 2
 //    before issuing f - 1;
-//  - S is a multiple of kFusedWarps and chunk g goes to consumer warp
-//    g % kFusedWarps, so slot s is always consumed by warp s % kFusedWarps,
+//  - S is a multiple of the consumer warp count W and chunk g goes to consumer
+//    warp g % W, so slot s is always consumed by warp s % W,
 //    which has consumed fill f - 1 (hence seen it land) before it waits for f.
 // Neither side waits on anything but earlier chunks, so the ring cannot
 // deadlock.
@@ -159,16 +163,18 @@ struct Ring {
 };
 
 // Named barrier of the consumer threads (the producer warp never joins it).
-__device__ __forceinline__ void csync() { asm volatile("bar.sync 1, %0;" ::"n"(kFusedThreads) : "memory"); }
+template <int NT>
+__device__ __forceinline__ void csync() { asm volatile("bar.sync 1, %0;" ::"n"(Blk<NT>::threads) : "memory"); }
 
 // Grid barrier over the consumers: thread 0 of each block adds 1 to a monotonic
 // counter (release) and polls it (acquire) until every block of this round has
 // arrived; `target` advances by the block count per barrier.  A wait failure
 // anywhere (`*err` of this block, a timeout here) is published in b->err and
 // makes every block's barrier return false.  Bounded by kWaitNs.
+template <int NT>
 __device__ __forceinline__ bool grid_sync(GridBar* b, unsigned nblocks, unsigned& target, const int* err,
                                           int* s_flag) {
-    csync();
+    csync<NT>();
     target += nblocks;
     if (nblocks == 1) {   // a one-block grid: the block barrier above is the whole barrier
         if (threadIdx.x == 0) {
@@ -176,7 +182,7 @@ __device__ __forceinline__ bool grid_sync(GridBar* b, unsigned nblocks, unsigned
             if (e) atomicExch(&b->err, 2);
             *s_flag = e;
         }
-        csync();
+        csync<NT>();
         return *s_flag == 0;
     }
     if (threadIdx.x == 0) {
@@ -199,7 +205,7 @@ __device__ __forceinline__ bool grid_sync(GridBar* b, unsigned nblocks, unsigned
         __threadfence();
         *s_flag = *((volatile int*)&b->err);
     }
-    csync();
+    csync<NT>();
     return *s_flag == 0;
 }
 
@@ -342,8 +348,9 @@ __device__ __forceinline__ bool produce_phase(const TM* __restrict__ M, int rows
 
 // Consumer side of one phase: part[c * pld + row] = chunk c of row `row` of M . xs
 // (chunk-major, so that the next phase's per-row sums load coalesced).  Warp w
-// takes the items whose slot is w modulo kFusedWarps (S is a multiple of it).
-template <typename TM, int TRI>
+// takes the items whose slot is w modulo the consumer warp count (S is a
+// multiple of it).
+template <typename TM, int TRI, int NT>
 __device__ __forceinline__ void gemv_ring(const Ring& R, RingPos& pos, int rows, int cols, long long ld,
                                           const TM* __restrict__ xs, TM* __restrict__ part, int pld,
                                           int* err) {
@@ -358,12 +365,13 @@ __device__ __forceinline__ void gemv_ring(const Ring& R, RingPos& pos, int rows,
     int b0, cnt;
     block_range<TRI>(rows, cols, CH, b0, cnt);
     const V* xv = reinterpret_cast<const V*>(xs);
-    const int first = (warp - pos.slot % kFusedWarps + kFusedWarps) % kFusedWarps;
+    constexpr int W = Blk<NT>::warps;
+    const int first = (warp - pos.slot % W + W) % W;
     if (first < cnt) {
         RingPos me = pos;
         me.advance(first, S);
         ItemWalk<TRI> w(rows, nc, CH, b0 + first);
-        for (int i = first; i < cnt; i += kFusedWarps) {
+        for (int i = first; i < cnt; i += W) {
             const int vbase = w.c * (CH / VN);
             const int slot = me.slot;
             if (!mbar_wait(&R.full[slot], (unsigned)(me.fill & 1))) *err = 1;
@@ -380,9 +388,9 @@ __device__ __forceinline__ void gemv_ring(const Ring& R, RingPos& pos, int rows,
             if (lane == 0) mbar_arrive(&R.empty[slot]);
             acc = warp_sum(acc);
             if (lane == 0) part[(long long)w.c * pld + w.row] = acc;
-            if (i + kFusedWarps < cnt) {
-                me.advance(kFusedWarps, S);
-                w.step(kFusedWarps);
+            if (i + W < cnt) {
+                me.advance(W, S);
+                w.step(W);
             }
         }
     }
@@ -429,14 +437,15 @@ __device__ __forceinline__ void sum_chunks4(const TM* __restrict__ part, int pld
 
 // Stage xs[j] for j < pad (zero from len on): rows are taken four per thread;
 // f(j, sum) turns a row's chunk sum into the staged value.
-template <typename TX, typename TM, int TRI, class F>
+template <int NT, typename TX, typename TM, int TRI, class F>
 __device__ __forceinline__ void stage_sum(TX* xs, const TM* part, int pld, int cols, int len, int pad, F f) {
     using AT = typename Acc<TM>::type;
-    for (int j0 = threadIdx.x; j0 < pad; j0 += 4 * kFusedThreads) {
+    constexpr int T = Blk<NT>::threads;
+    for (int j0 = threadIdx.x; j0 < pad; j0 += 4 * T) {
         int j[4];
         AT sm[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) j[u] = j0 + u * kFusedThreads;
+        for (int u = 0; u < 4; ++u) j[u] = j0 + u * T;
         sum_chunks4<TM, TRI, AT>(part, pld, cols, j, len, sm);
 #pragma unroll
         for (int u = 0; u < 4; ++u)
@@ -447,17 +456,18 @@ __device__ __forceinline__ void stage_sum(TX* xs, const TM* part, int pld, int c
 // stage_sum with an operand loaded before the partials: pre(j) is issued for the
 // four rows together with their partial loads, and f(j, sum, pre(j)) makes the
 // staged value, so a loop-invariant vector costs no extra round trip.
-template <typename TX, typename TM, int TRI, class P, class F>
+template <int NT, typename TX, typename TM, int TRI, class P, class F>
 __device__ __forceinline__ void stage_sum_pre(TX* xs, const TM* part, int pld, int cols, int len, int pad, P pre,
                                               F f) {
     using AT = typename Acc<TM>::type;
-    for (int j0 = threadIdx.x; j0 < pad; j0 += 4 * kFusedThreads) {
+    constexpr int T = Blk<NT>::threads;
+    for (int j0 = threadIdx.x; j0 < pad; j0 += 4 * T) {
         int j[4];
         AT sm[4];
         decltype(pre(0)) pv[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            j[u] = j0 + u * kFusedThreads;
+            j[u] = j0 + u * T;
             pv[u] = (j[u] < len) ? pre(j[u]) : decltype(pre(0))(0);
         }
         sum_chunks4<TM, TRI, AT>(part, pld, cols, j, len, sm);
@@ -468,20 +478,20 @@ __device__ __forceinline__ void stage_sum_pre(TX* xs, const TM* part, int pld, i
 }
 
 // Consumer-wide fixed-order sum, result broadcast to every consumer thread.
-template <typename AT>
+template <int NT, typename AT>
 __device__ __forceinline__ AT block_allsum(AT v, AT* sh) {
     v = warp_sum(v);
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     if (l == 0) sh[w] = v;
-    csync();
+    csync<NT>();
     if (threadIdx.x < 32) {
-        AT r = (l < kFusedWarps) ? sh[l] : AT(0);
+        AT r = (l < Blk<NT>::warps) ? sh[l] : AT(0);
         r = warp_sum(r);
         if (l == 0) sh[32] = r;
     }
-    csync();
+    csync<NT>();
     v = sh[32];
-    csync();
+    csync<NT>();
     return v;
 }
 
@@ -554,8 +564,9 @@ __device__ void pcg_producer(const FusedArgs<TO, TP>& a, const Ring& R) {
 // st->tol2 = tol^2 |rhs|^2, st->maxit.  Shared memory: the staged vector
 // (xs_bytes), three m2-vectors in TO (q = K_F p, r and p of the current
 // iteration), then the ring.
-template <typename TO, typename TP, int PC>
-__global__ void __launch_bounds__(kFusedBlock, 1) pcg_fused_kernel(const FusedArgs<TO, TP> a) {
+template <typename TO, typename TP, int PC, int NT>
+__global__ void __launch_bounds__(NT, NT == kSmallBlock ? 2 : 1) pcg_fused_kernel(const FusedArgs<TO, TP> a) {
+    constexpr int kFusedThreads = Blk<NT>::threads;
     PCG_COUNT_KERNEL();
     extern __shared__ __align__(128) unsigned char pcg_smem[];
     TO* xs = reinterpret_cast<TO*>(pcg_smem);
@@ -612,13 +623,13 @@ __global__ void __launch_bounds__(kFusedBlock, 1) pcg_fused_kernel(const FusedAr
     RingPos g;   // ring position of the next chunk
     // every consumer exit passes here: the producer stops issuing and drains
     auto leave = [&]() {
-        csync();
+        csync<NT>();
         if (tid == 0) {
             if (s_err) atomicExch(&a.bar->err, 2);
             *R.stop = 1;
         }
     };
-    auto gsync = [&]() { return grid_sync(a.bar, nblocks, target, &s_err, &s_flag); };
+    auto gsync = [&]() { return grid_sync<NT>(a.bar, nblocks, target, &s_err, &s_flag); };
 
     AT rz = (AT)__ldcg(&a.st->rz_cur);
     const double tol2 = __ldcg(&a.st->tol2);
@@ -634,49 +645,49 @@ __global__ void __launch_bounds__(kFusedBlock, 1) pcg_fused_kernel(const FusedAr
         pcs[j] = __ldcg(pc + j);
         rc[j] = __ldcg(rcur + j);
     }
-    csync();
+    csync<NT>();
     for (int j = tid; j < padO_m2; j += kFusedThreads) xs[j] = (j < m2) ? pcs[j] : TO(0);
-    csync();
+    csync<NT>();
 
     while (true) {
         mark(it, 0);
         // ---- P1 (a6): u = C' p
-        gemv_ring<TO, TRI_NONE>(R, g, n, m2, a.ldCWT, xs, a.PU, a.ldU, &s_err);
+        gemv_ring<TO, TRI_NONE, NT>(R, g, n, m2, a.ldCWT, xs, a.PU, a.ldU, &s_err);
         mark(it, 11);
         if (!gsync()) { leave(); return; }
         mark(it, 1);
         // ---- P2 (a7, forward solve with L): z1 = R^{-T} u, Et u (z2 = -Et u)
-        stage_sum<TO, TO, TRI_NONE>(xs, a.PU, a.ldU, m2, n, padO_n, [&](int, AT v) { return (TO)v; });
-        csync();
+        stage_sum<NT, TO, TO, TRI_NONE>(xs, a.PU, a.ldU, m2, n, padO_n, [&](int, AT v) { return (TO)v; });
+        csync<NT>();
         mark(it, 12);
-        gemv_ring<TO, TRI_LOWER>(R, g, n, n, a.ldWH, xs, a.PZ1, a.ldZ1, &s_err);
-        if (m1 > 0) gemv_ring<TO, TRI_NONE>(R, g, m1, n, a.ldEt, xs, a.PZ2, a.ldZ2, &s_err);
+        gemv_ring<TO, TRI_LOWER, NT>(R, g, n, n, a.ldWH, xs, a.PZ1, a.ldZ1, &s_err);
+        if (m1 > 0) gemv_ring<TO, TRI_NONE, NT>(R, g, m1, n, a.ldEt, xs, a.PZ2, a.ldZ2, &s_err);
         mark(it, 13);
         if (!gsync()) { leave(); return; }
         mark(it, 2);
         // ---- P3 (a7, back solve with L'): y = R^{-1} z1 + Et' z2
-        stage_sum<TO, TO, TRI_LOWER>(xs, a.PZ1, a.ldZ1, n, n, padO_n, [&](int, AT v) { return (TO)v; });
+        stage_sum<NT, TO, TO, TRI_LOWER>(xs, a.PZ1, a.ldZ1, n, n, padO_n, [&](int, AT v) { return (TO)v; });
         if (m1 > 0)
-            stage_sum<TO, TO, TRI_NONE>(xs2, a.PZ2, a.ldZ2, n, m1, padO_m1, [&](int, AT v) { return (TO)(-v); });
-        csync();
+            stage_sum<NT, TO, TO, TRI_NONE>(xs2, a.PZ2, a.ldZ2, n, m1, padO_m1, [&](int, AT v) { return (TO)(-v); });
+        csync<NT>();
         mark(it, 14);
-        gemv_ring<TO, TRI_UPPER>(R, g, n, n, a.ldWHT, xs, a.PY, a.ldY, &s_err);
-        if (m1 > 0) gemv_ring<TO, TRI_NONE>(R, g, n, m1, a.ldEtT, xs2, a.PT, a.ldT, &s_err);
+        gemv_ring<TO, TRI_UPPER, NT>(R, g, n, n, a.ldWHT, xs, a.PY, a.ldY, &s_err);
+        if (m1 > 0) gemv_ring<TO, TRI_NONE, NT>(R, g, n, m1, a.ldEtT, xs2, a.PT, a.ldT, &s_err);
         mark(it, 15);
         if (!gsync()) { leave(); return; }
         mark(it, 5);
         // ---- P4 (a8): q = D p + C y
         if (m1 > 0) {
-            stage_sum<TO, TO, TRI_NONE>(xs, a.PT, a.ldT, m1, n, padO_n, [&](int, AT v) { return (TO)v; });
-            csync();
-            stage_sum<TO, TO, TRI_UPPER>(xs, a.PY, a.ldY, n, n, padO_n,
+            stage_sum<NT, TO, TO, TRI_NONE>(xs, a.PT, a.ldT, m1, n, padO_n, [&](int, AT v) { return (TO)v; });
+            csync<NT>();
+            stage_sum<NT, TO, TO, TRI_UPPER>(xs, a.PY, a.ldY, n, n, padO_n,
                                          [&](int j, AT v) { return (TO)(v + (AT)xs[j]); });
         } else {
-            stage_sum<TO, TO, TRI_UPPER>(xs, a.PY, a.ldY, n, n, padO_n, [&](int, AT v) { return (TO)v; });
+            stage_sum<NT, TO, TO, TRI_UPPER>(xs, a.PY, a.ldY, n, n, padO_n, [&](int, AT v) { return (TO)v; });
         }
-        csync();
+        csync<NT>();
         mark(it, 16);
-        gemv_ring<TO, TRI_NONE>(R, g, m2, n, a.ldCW, xs, a.PQ, a.ldQ, &s_err);
+        gemv_ring<TO, TRI_NONE, NT>(R, g, m2, n, a.ldCW, xs, a.PQ, a.ldQ, &s_err);
         mark(it, 17);
         if (!gsync()) { leave(); return; }
         mark(it, 6);
@@ -684,13 +695,13 @@ __global__ void __launch_bounds__(kFusedBlock, 1) pcg_fused_kernel(const FusedAr
         // ---- P5 (a10): q = D p + C y (cached), alpha = r'z / p'q, x += alpha p, r -= alpha q
         // (p'q is summed while q is staged: each thread takes its rows in increasing order)
         AT pq = AT(0);
-        stage_sum_pre<TO, TO, TRI_NONE>(qc, a.PQ, a.ldQ, n, m2, m2, [&](int j) { return __ldg(a.D + j); },
+        stage_sum_pre<NT, TO, TO, TRI_NONE>(qc, a.PQ, a.ldQ, n, m2, m2, [&](int j) { return __ldg(a.D + j); },
                                         [&](int j, AT v, TO dj) {
                                             const TO q = (TO)fma((AT)dj, (AT)pcs[j], v);
                                             pq = fma((AT)pcs[j], (AT)q, pq);
                                             return q;
                                         });
-        pq = block_allsum(pq, sh);
+        pq = block_allsum<NT>(pq, sh);
         // breakdown (p'q <= 0 or not finite): stop with the last iterate untouched
         if (!(pq > AT(0)) || !isfinite(pq)) { done = 3; break; }
         const AT alpha = rz / pq;
@@ -718,7 +729,7 @@ __global__ void __launch_bounds__(kFusedBlock, 1) pcg_fused_kernel(const FusedAr
         }
         if (PC == PC_H_K)
             for (int j = padO_m2 + tid; j < padP_m2; j += kFusedThreads) xp[j] = TP(0);
-        rr = block_allsum(rrp, sh);
+        rr = block_allsum<NT>(rrp, sh);
         ++it;
         const bool finite = isfinite(rr) && isfinite(pq);
         if (!finite) { done = 3; break; }
@@ -728,31 +739,31 @@ __global__ void __launch_bounds__(kFusedBlock, 1) pcg_fused_kernel(const FusedAr
 
         AT rz_new;
         if (PC == PC_H_K) {
-            csync();
+            csync<NT>();
             // ---- P6 (a9): v = W rs, z = Sg W' v
-            gemv_ring<TP, TRI_LOWER>(R, g, m2, m2, a.ldWP, xp, a.PV, a.ldV, &s_err);
+            gemv_ring<TP, TRI_LOWER, NT>(R, g, m2, m2, a.ldWP, xp, a.PV, a.ldV, &s_err);
             mark(it - 1, 18);
             if (!gsync()) { leave(); return; }
             mark(it - 1, 8);
-            stage_sum<TP, TP, TRI_LOWER>(xp, a.PV, a.ldV, m2, m2, padP_m2, [&](int, typename Acc<TP>::type v) { return (TP)v; });
-            csync();
+            stage_sum<NT, TP, TP, TRI_LOWER>(xp, a.PV, a.ldV, m2, m2, padP_m2, [&](int, typename Acc<TP>::type v) { return (TP)v; });
+            csync<NT>();
             mark(it - 1, 19);
-            gemv_ring<TP, TRI_UPPER>(R, g, m2, m2, a.ldWP, xp, a.PZ, a.ldZ, &s_err);
+            gemv_ring<TP, TRI_UPPER, NT>(R, g, m2, m2, a.ldWP, xp, a.PZ, a.ldZ, &s_err);
             mark(it - 1, 20);
             if (!gsync()) { leave(); return; }
             mark(it - 1, 9);
             // z into the q cache (q is no longer needed), then r'z
             // (r'z is summed while z is staged, rows in increasing order per thread)
             rzp = AT(0);
-            stage_sum_pre<TO, TP, TRI_UPPER>(qc, a.PZ, a.ldZ, m2, m2, m2, [&](int j) { return __ldg(a.sg + j); },
+            stage_sum_pre<NT, TO, TP, TRI_UPPER>(qc, a.PZ, a.ldZ, m2, m2, m2, [&](int j) { return __ldg(a.sg + j); },
                                              [&](int j, typename Acc<TP>::type v, TP sj) {
                                                  const TO z = (TO)((AT)sj * (AT)v);
                                                  rzp = fma((AT)rc[j], (AT)z, rzp);
                                                  return z;
                                              });
-            rz_new = block_allsum(rzp, sh);
+            rz_new = block_allsum<NT>(rzp, sh);
         } else {
-            rz_new = block_allsum(rzp, sh);
+            rz_new = block_allsum<NT>(rzp, sh);
         }
         // ---- beta, p = z + beta p (staged as the next P1 input; shared-memory only)
         const AT beta = rz_new / rz;
@@ -771,7 +782,7 @@ __global__ void __launch_bounds__(kFusedBlock, 1) pcg_fused_kernel(const FusedAr
             }
             xs[j] = v;
         }
-        csync();
+        csync<NT>();
         mark(it - 1, 10);
         // swap the double buffers (global copies; the shared caches already hold the new values)
         TO* t1 = pc; pc = pn; pn = t1;
