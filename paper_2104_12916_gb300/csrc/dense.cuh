@@ -177,6 +177,9 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(T* A, long long lda, T*
         a[i][j] = (j <= i) ? CT(A[(k0 + i) * lda + k0 + j]) : CT(0);
     }
     __syncthreads();
+    // right-looking: scale column j, then update the trailing lower triangle;
+    // thread (ty, tx) of a 16 x 16 layout takes rows ty + 16 r and columns tx + 16 c
+    const int tx = tid & 15, ty = tid >> 4;
     for (int j = 0; j < kb; ++j) {
         if (tid == 0) {
             CT d = a[j][j];
@@ -196,25 +199,28 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(T* A, long long lda, T*
         const CT inv = CT(1) / piv;
         for (int i = j + 1 + tid; i < kb; i += 256) a[i][j] *= inv;
         __syncthreads();
-        const int rem = kb - j - 1;
-        for (int e = tid; e < rem * rem; e += 256) {
-            const int i = j + 1 + e / rem, l = j + 1 + e % rem;
-            if (l <= i) a[i][l] -= a[i][j] * a[l][j];
+        for (int i = j + 1 + ty; i < kb; i += 16) {
+            const CT aij = a[i][j];
+            for (int l = j + 1 + tx; l <= i; l += 16) a[i][l] -= aij * a[l][j];
         }
         __syncthreads();
     }
-    // W = L^{-1}: thread t solves L w_t = e_t (column t) by forward substitution.
-    if (tid < kb) {
-        const int t = tid;
-        for (int i = 0; i < t; ++i) w[i][t] = CT(0);
-        w[t][t] = CT(1) / a[t][t];
-        for (int i = t + 1; i < kb; ++i) {
-            CT s = CT(0);
-            for (int k = t; k < i; ++k) s += a[i][k] * w[k][t];
-            w[i][t] = -s / a[i][i];
+    // W = L^{-1}, row by row: w[i][i] = 1 / l_ii and, for t < i,
+    // w[i][t] = -(sum_{k=t}^{i-1} l_ik w[k][t]) / l_ii.  Four threads share a
+    // column t (k split four ways, shuffle-reduced), so all 256 threads work.
+    const int t = tid >> 2, q = tid & 3;
+    for (int i = 0; i < kb; ++i) {
+        CT sum = CT(0);
+        if (t < i)
+            for (int k = t + q; k < i; k += 4) sum += a[i][k] * w[k][t];
+        sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+        sum += __shfl_xor_sync(0xffffffffu, sum, 2);
+        if (q == 0) {
+            if (t < i) w[i][t] = -sum / a[i][i];
+            else if (t == i) w[i][i] = CT(1) / a[i][i];
         }
+        __syncthreads();
     }
-    __syncthreads();
     for (int e = tid; e < kb * kb; e += 256) {
         const int i = e / kb, j = e % kb;
         A[(k0 + i) * lda + k0 + j] = (j <= i) ? T(a[i][j]) : T(0);

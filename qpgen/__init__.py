@@ -23,6 +23,14 @@ Workloads (the shapes the method is measured on):
 * ``sparse_C``: 8 nonzeros per row, column indices drawn without replacement,
   values N(0,1), returned as CSR.
 * ``tiny_qp``: the same recipe at n <= 6, m2 <= 10 for brute-force checks.
+* ``syqp``: the paper's synthetic family SyQP^n_{m1} (Sec. 6, Test problems):
+  simple bounds x >= 0 (C = I, d = 0); H block diagonal with 4 x 4 blocks M'M,
+  M ~ U[0,1); A full rank and banded with band entries ~ U[0,1); c ~ U[0,1).
+  The band width and the draw of b are not given there: row i of A covers the
+  ``band`` columns from s_i = floor(i (n - w + 1) / m1), w = min(band, n - m1 + 1)
+  (strictly increasing starts, so A has full row rank), and b = A x0 with
+  x0 ~ U(0.5, 1.5) so that a strictly feasible point exists.  Draw order: the
+  H blocks, the band of A, x0, c.
 """
 from __future__ import annotations
 
@@ -33,7 +41,7 @@ import numpy as np
 
 __all__ = [
     "QP", "dense_qp", "config_qp", "batch_dims", "serving_dims", "tiny_qp",
-    "CONFIGS", "pcg_inputs", "arrival_times",
+    "CONFIGS", "pcg_inputs", "arrival_times", "syqp",
 ]
 
 
@@ -218,3 +226,24 @@ def pcg_inputs(m2: int, seed: int, d_lo: float = 1e-2, d_hi: float = 1e2):
     D = _log_uniform(rng, d_lo, d_hi, m2)
     rhs = rng.standard_normal(m2)
     return D, rhs
+
+
+def syqp(n: int, m1: int, seed: int = 0, band: int = 3) -> QP:
+    """SyQP^n_{m1} of the paper's synthetic family (see the module docstring)."""
+    if not (1 <= m1 <= n):
+        raise ValueError("SyQP needs 1 <= m1 <= n")
+    rng = np.random.default_rng(3_000_000 + seed)
+    H = np.zeros((n, n))
+    for k in range(0, n, 4):
+        b = min(4, n - k)
+        M = rng.uniform(0.0, 1.0, (b, b))
+        H[k:k + b, k:k + b] = M.T @ M
+    w = min(band, n - m1 + 1)
+    A = np.zeros((m1, n))
+    for i in range(m1):
+        s0 = (i * (n - w + 1)) // m1
+        A[i, s0:s0 + w] = rng.uniform(0.0, 1.0, w)
+    x0 = rng.uniform(0.5, 1.5, n)
+    c = rng.uniform(0.0, 1.0, n)
+    C = np.eye(n)
+    return QP(H=H, c=c, A=A, b=A @ x0, C=C, d=np.zeros(n), x0=x0, name=f"syqp{n}_{m1}_s{seed}")
