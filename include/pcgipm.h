@@ -64,7 +64,9 @@ enum qp_precision {
     QP_PREC_FP32 = 1      /* mixed: C copies, K0 factor and PCG in FP32 until FP64 refinement
                              contracts by less than 4x per sweep, then in FP64 (a second, FP64
                              factor of K0); P_H in FP32 until its factorization needs a shift, then
-                             in FP64; FP64 residuals, refinement, step logic */
+                             in FP64; FP64 residuals, refinement, step logic.  With mixed_fallback,
+                             a QP whose FP32 K0 factor meets a pivot below FP32 resolution is
+                             factored and solved in FP64 from the start */
 };
 
 enum qp_precond {

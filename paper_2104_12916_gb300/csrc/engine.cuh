@@ -164,6 +164,7 @@ public:
     bool own_stream = false;
     bool factored = false;
     bool f64 = false;       // QP_PREC_FP64
+    bool all64 = false;     // QP_PREC_FP32 whose K0 factor needed FP64 pivots: the QP runs in FP64
     bool use64 = false;     // operator currently in FP64
     bool pc64 = false;      // preconditioner currently in FP64
     DevArena arena;
@@ -555,10 +556,26 @@ public:
     void factor() {
         if (factored) return;
         PCG_CK(cudaEventRecord(evA, s));
-        if (f64) factor_op<double>(); else factor_op<float>();
+        if (f64) {
+            factor_op<double>();
+        } else {
+            try {
+                factor_op<float>();
+            } catch (const QpError& e) {
+                // A pivot of the FP32 factor of H or of A H^{-1} A' fell below FP32
+                // resolution relative to its diagonal (ill-conditioned H or F_H): with
+                // mixed_fallback the QP is factored and solved in FP64, which decides
+                // whether the matrix is really singular or indefinite.
+                if (!((e.code == QP_ESINGULAR || e.code == QP_ENOTCONVEX) && allow_pc64)) throw;
+                if (verbose) std::fprintf(stderr, "  FP32 K0 factor failed (%d): FP64 from the start\n", e.code);
+                factor_op<double>();
+                all64 = true;
+                use64 = pc64 = true;
+            }
+        }
         const int pc = resolve_pc(opt.precond, n, m1);
         if (pc_kind(pc) == PC_H_K) {
-            if (f64) ensure_T<double>(pc); else ensure_T<float>(pc);
+            if (f64 || all64) ensure_T<double>(pc); else ensure_T<float>(pc);
         }
         PCG_CK(cudaEventRecord(evB, s));
         PCG_CK(cudaEventSynchronize(evB));
@@ -1405,8 +1422,9 @@ public:
         stats.ipm_iters = 0; stats.pcg_iters_total = 0; stats.newton_solves = 0; stats.refine_sweeps = 0;
         stats.t_pcg_ms = 0; stats.t_precond_ms = 0; stats.op64_solves = 0; stats.op64_switch_iter = -1;
         stats.pc64_switch_iter = -1; stats.pc_switch_iter = -1;
-        use64 = f64;
-        pc64 = f64;
+        use64 = f64 || all64;
+        pc64 = f64 || all64;
+        if (all64) { stats.op64_switch_iter = 0; stats.pc64_switch_iter = 0; }
         ipm_k = 0;
         ipm_pc = resolve_pc(opt.precond, n, m1);
         stats.precond_used = ipm_pc;
