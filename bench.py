@@ -263,6 +263,41 @@ def run_ours(args):
                           f"{by_it / 1e6:.1f} MB algorithmic, {ms_it * 1e3:.1f} us",
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback"}
 
+    # ---- the same path with pcg_form = 1 (K_F through B = L^-1[C'; 0], two matrix phases)
+    o = opts(B.QP_PREC_FP32)
+    o.mixed_fallback, o.pcg_form = 0, 1
+    h = B.qp_create(Hd, cd, Ad, bd, Cd, dd, o)
+    B.qp_factor_K0(h)
+    ms_w = B.qp_time_pcg_iteration(h, Dmid, precond=B.QP_PC_AUTO, warmup=16, iters=128)
+    by_w = B.qp_pcg_bytes_per_iter(h, B.QP_PC_AUTO)
+    B.qp_destroy(h)
+    def step_w(out):
+        ow = opts(B.QP_PREC_FP32)
+        ow.pcg_form = 1
+        hw = B.qp_create(Hd, cd, Ad, bd, Cd, dd, ow)
+        try:
+            st_, f_, its_, pits_ = B.qp_ipm_solve(hw, xd, allow=(B.QP_OK, B.QP_EMAXIT, B.QP_ENUMERIC))
+            out.append(dict(status=st_, f=f_, ipm=its_, pcg=pits_))
+        finally:
+            B.qp_destroy(hw)
+    step_w([])
+    torch.cuda.synchronize()
+    flush.fill_(1.0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    rw = []
+    e0.record(stream)
+    step_w(rw)
+    e1.record(stream)
+    e1.synchronize()
+    ms_wsolve = e0.elapsed_time(e1)
+    ok_w = abs(rw[0]["f"] - gold["f"]) / max(abs(gold["f"]), 1.0) <= 1e-6 and rw[0]["status"] == 0
+    wform = {"what": "pcg_form=1: K_F p = D p + B1'(B1 p) - B2'(B2 p), B = L^-1[C'; 0] formed once per QP",
+             "pcg_iteration_us": round(ms_w * 1e3, 1), "algorithmic_MB": round(by_w / 1e6, 1),
+             "achieved_GBps": round(by_w / (ms_w * 1e-3) / 1e9, 1),
+             "frac": round(by_w / (ms_w * 1e-3) / 1e9 / peak, 4),
+             "qps_per_s": round((1.0 if ok_w else 0.0) / (ms_wsolve / 1e3), 4), "ms_per_solve": round(ms_wsolve, 1),
+             "ipm_iters": rw[0]["ipm"], "pcg_iters": rw[0]["pcg"], "obj_rel_err": abs(rw[0]["f"] - gold["f"]) / abs(gold["f"])}
+
     # ---- end to end through host buffers (H2D of the inputs and D2H of x inside)
     e2e_ms = 0.0
     xh = np.zeros(qp.n)
@@ -303,7 +338,7 @@ def run_ours(args):
             "fp64": {"value": round(value64, 4), "unit": "QPs/s", "ms_per_step": round(total64 / max(1, args.fp64_steps), 2),
                      "dtype": "f64", "solved": f"{sum(ok64)}/{len(ok64)}",
                      "ipm_iters": [r["ipm"] for r in res64], "pcg_iters": [r["pcg"] for r in res64]},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "roofline": roofline, "wform": wform, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clk.summary(),
         }
         print(json.dumps(line), flush=True)

@@ -113,6 +113,12 @@ typedef struct {
                              every reduction has a fixed order independent of the grid. */
     int blocking_wait;    /* 1: host waits on the solver's stream yield the CPU instead of spinning
                              (many QPs in flight on more host threads than cores); default 0 */
+    int pcg_form;         /* how the persistent PCG kernel applies K_F.  0 (default): the implicit
+                             product of Sec. 5.2 (C'p, the forward and back solves with the K0
+                             factor, C y; four matrix phases).  1: the same product through
+                             B = L^{-1}[C'; 0] = [R^{-T} C'; Et C'], formed once per QP:
+                             K_F p = D p + B1'(B1 p) - B2'(B2 p) (two matrix phases; 2 (n + m1) m2
+                             elements per iteration instead of 2 m2 n + n^2 + 2 m1 n) */
     void *stream;         /* cudaStream_t, or NULL for a library-created stream */
 } qp_opts;
 

@@ -37,7 +37,7 @@ class qp_opts(ct.Structure):
         ("max_ipm", ct.c_int), ("max_pcg", ct.c_int), ("refine_max", ct.c_int),
         ("pcg_tol", ct.c_double), ("refine_tol", ct.c_double), ("tol_feas", ct.c_double),
         ("tol_mu", ct.c_double), ("pcg_check_every", ct.c_int), ("mixed_fallback", ct.c_int),
-        ("pcg_blocks", ct.c_int), ("blocking_wait", ct.c_int),
+        ("pcg_blocks", ct.c_int), ("blocking_wait", ct.c_int), ("pcg_form", ct.c_int),
         ("stream", ct.c_void_p),
     ]
 
@@ -344,9 +344,10 @@ class QP:
 
     @classmethod
     def from_qpgen(cls, q, opts=None):
-        A = q.A if q.m1 else None
-        b = q.b if q.m1 else None
-        return cls(np.ascontiguousarray(q.H), q.c, A, b, np.ascontiguousarray(q.C_dense()), q.d, opts)
+        c = lambda a: np.ascontiguousarray(a, dtype=np.float64)
+        A = c(q.A) if q.m1 else None
+        b = c(q.b) if q.m1 else None
+        return cls(c(q.H), c(q.c), A, b, c(q.C_dense()), c(q.d), opts)
 
     def factor(self):
         qp_factor_K0(self.h)

@@ -135,6 +135,9 @@ struct Op {
     Mat<TO> Gt, GtT;   // L_S^{-1} A R^{-1} and its transpose, L_S L_S' = A H^{-1} A'
     Mat<TO> Et, EtT;   // Gt R^{-T} = L_S^{-1} A H^{-1} (the (2,1) block of L^{-1}) and its transpose
     Mat<TO> WS, WST;   // L_S^{-1} (lower) and L_S^{-T} (upper)
+    Mat<TO> BW, BWT;   // pcg_form 1: B = L^{-1}[C'; 0] = [R^{-T} C'; Et C'] ((n+m1) x m2) and B'
+    TO* PW = nullptr;  // pcg_form 1: chunk partials of B p
+    int ldW = 0;
     TO *px = nullptr, *pr, *pz, *pp, *pq, *pu, *pz1, *pz2, *pt, *py, *prhs, *pD, *pDinv;
     TO *ku, *kw, *ke, *kz1, *kz2, *kt, *ka, *kmb, *wa, *wg;
     TO *pr1, *pp1;                       // second buffers of r and p (fused kernel)
@@ -292,6 +295,8 @@ public:
             if (copyC) t += mat(m2, n, es) + mat(n, m2, es);
             t += 2 * mat(n, n, es);
             if (m1) t += 2 * mat(m1, m1, es) + 2 * mat(m1, n, es) + 2 * mat(n, m1, es);
+            if (o.pcg_form == 1)
+                t += mat(n + m1, m2, es) + mat(m2, n + m1, es) + (size_t)(n + m1) * ncs(m2) * es + 256;
             t += mat(n, n, es) + 2 * mat(m1, n, es) + mat(m1, m1, es);   // factor scratch
             return t;
         };
@@ -304,7 +309,7 @@ public:
         const bool ph = o.precond != QP_PC_PL && o.precond != QP_PC_NONE;
         if (fp32) {
             b += op(4, true);
-            if (o.mixed_fallback) b += op(8, false);
+            if (o.mixed_fallback || o.pcg_form == 1) b += op(8, false);   // FP64 factor (W-form: B from it)
             if (ph) b += pc(4) + (o.mixed_fallback ? pc(8) : 0);
         } else {
             b += op(8, false);
@@ -470,7 +475,13 @@ public:
             o.ldU = n; o.ldZ1 = n; o.ldZ2 = std::max(m1, 1); o.ldT = n; o.ldY = n; o.ldQ = m2;
             o.PU = arena.alloc<TO>(n * ncs(m2)); o.PZ1 = arena.alloc<TO>(n * ncs(n));
             o.PZ2 = arena.alloc<TO>(std::max(m1, 1) * ncs(n)); o.PT = arena.alloc<TO>(n * ncs(m1));
-            o.PY = arena.alloc<TO>(n * ncs(n)); o.PQ = arena.alloc<TO>(m2 * ncs(n));
+            o.PY = arena.alloc<TO>(n * ncs(n)); o.PQ = arena.alloc<TO>(m2 * ncs(n + m1));
+            if (opt.pcg_form == 1) {
+                o.BW.alloc(arena, n + m1, m2);
+                o.BWT.alloc(arena, m2, n + m1);
+                o.ldW = n + m1;
+                o.PW = arena.alloc<TO>((size_t)(n + m1) * ncs(m2));
+            }
             if constexpr (is64) {
                 o.CW.p = C.p; o.CW.rows = m2; o.CW.cols = n; o.CW.ld = C.ld;
                 o.CWT.p = CT.p; o.CWT.rows = n; o.CWT.cols = m2; o.CWT.ld = CT.ld;
@@ -540,6 +551,31 @@ public:
             e.C = o.Et.p; e.ldc = o.Et.ld; e.alpha = TO(1); e.beta = TO(0);
             gemm<TO>(e, s);
             transpose<TO>(o.Et.p, o.Et.ld, o.EtT.p, o.EtT.ld, m1, n, s);
+        }
+        if (opt.pcg_form == 1 && !is64) {
+            // B is formed from the FP64 factor and rounded once to FP32, so its entries
+            // carry only their final rounding (an FP32 product over n terms of the FP32
+            // inverse factor would add about sqrt(n) u32 cond(R) relative error)
+            factor_op<double>();
+            convert2d<double, TO>(o64.BW.p, o64.BW.ld, o.BW.p, o.BW.ld, n + m1, m2, s);
+            transpose<TO>(o.BW.p, o.BW.ld, o.BWT.p, o.BWT.ld, n + m1, m2, s);
+        } else if (opt.pcg_form == 1) {
+            // B = L^{-1}[C'; 0]: B1 = R^{-T} C' (n x m2), B2 = Et C' (m1 x m2), and B'
+            GemmArgs<TO> b1{};
+            b1.M = n; b1.N = m2; b1.K = n;
+            b1.A = o.WH.p; b1.sai = o.WH.ld; b1.sak = 1; b1.a_tri = TRI_LOWER;
+            b1.B = o.CWT.p; b1.sbk = o.CWT.ld; b1.sbj = 1;
+            b1.C = o.BW.p; b1.ldc = o.BW.ld; b1.alpha = TO(1); b1.beta = TO(0);
+            gemm<TO>(b1, s);
+            if (m1) {
+                GemmArgs<TO> b2{};
+                b2.M = m1; b2.N = m2; b2.K = n;
+                b2.A = o.Et.p; b2.sai = o.Et.ld; b2.sak = 1;
+                b2.B = o.CWT.p; b2.sbk = o.CWT.ld; b2.sbj = 1;
+                b2.C = o.BW.p + (long long)n * o.BW.ld; b2.ldc = o.BW.ld; b2.alpha = TO(1); b2.beta = TO(0);
+                gemm<TO>(b2, s);
+            }
+            transpose<TO>(o.BW.p, o.BW.ld, o.BWT.p, o.BWT.ld, n + m1, m2, s);
         }
         PCG_CK(cudaMemcpyAsync(h_info, d_info, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
         cudaFreeAsync(Hw, s);
@@ -810,6 +846,8 @@ public:
         fa.n = n; fa.m1 = m1; fa.m2 = m2;
         fa.CWT = o.CWT.p; fa.ldCWT = o.CWT.ld; fa.WH = o.WH.p; fa.ldWH = o.WH.ld;
         fa.Et = o.Et.p; fa.ldEt = o.Et.ld; fa.EtT = o.EtT.p; fa.ldEtT = o.EtT.ld;
+        fa.wform = (opt.pcg_form == 1) ? 1 : 0;
+        fa.BW = o.BW.p; fa.ldBW = o.BW.ld; fa.BWT = o.BWT.p; fa.ldBWT = o.BWT.ld; fa.PW = o.PW; fa.ldPW = o.ldW;
         fa.WHT = o.WHT.p; fa.ldWHT = o.WHT.ld; fa.CW = o.CW.p; fa.ldCW = o.CW.ld;
         fa.WPl = P.WPl.p; fa.WPu = P.WPu.p; fa.ldWP = P.WPl.ld; fa.sg = P.sg;
         fa.D = o.pD; fa.Dinv = o.pDinv; fa.x = o.px;
@@ -1125,7 +1163,8 @@ public:
     double bytes_per_iter(int pc) const {
         pc = resolve_pc(pc, n, m1);
         const double eo = use64 ? 8.0 : 4.0, ep = pc64 ? 8.0 : 4.0;
-        const double bo = 2.0 * m2 * n + (double)n * (n + 1) + 2.0 * m1 * n;
+        const double bo = (opt.pcg_form == 1 && use_fused()) ? 2.0 * (n + m1) * m2
+                                                            : 2.0 * m2 * n + (double)n * (n + 1) + 2.0 * m1 * n;
         const double bp = pc_kind(pc) == PC_H_K ? (double)m2 * (m2 + 1) : 0.0;
         const double vec_el = 12.0 * m2 + 8.0 * n + 4.0 * m1;
         return bo * eo + bp * ep + vec_el * eo;

@@ -501,6 +501,12 @@ struct FusedArgs {
     // operator (precision TO)
     const TO *CWT, *WH, *Et, *EtT, *WHT, *CW;
     long long ldCWT, ldWH, ldEt, ldEtT, ldWHT, ldCW;
+    // pcg_form 1: B = L^{-1}[C'; 0] ((n+m1) x m2) and B', partials of B p
+    int wform;
+    const TO *BW, *BWT;
+    long long ldBW, ldBWT;
+    TO* PW;
+    int ldPW;
     // preconditioner (precision TP)
     const TP *WPl, *WPu;
     long long ldWP;
@@ -539,12 +545,17 @@ __device__ void pcg_producer(const FusedArgs<TO, TP>& a, const Ring& R) {
     const int n = a.n, m1 = a.m1, m2 = a.m2;
     RingPos g;
     while (!*R.stop) {   // (a block may own no chunk of any phase: it polls the stop flag here)
-        if (!produce_phase<TO, TRI_NONE>(a.CWT, n, m2, a.ldCWT, R, g)) break;
-        if (!produce_phase<TO, TRI_LOWER>(a.WH, n, n, a.ldWH, R, g)) break;
-        if (m1 > 0 && !produce_phase<TO, TRI_NONE>(a.Et, m1, n, a.ldEt, R, g)) break;
-        if (!produce_phase<TO, TRI_UPPER>(a.WHT, n, n, a.ldWHT, R, g)) break;
-        if (m1 > 0 && !produce_phase<TO, TRI_NONE>(a.EtT, n, m1, a.ldEtT, R, g)) break;
-        if (!produce_phase<TO, TRI_NONE>(a.CW, m2, n, a.ldCW, R, g)) break;
+        if (a.wform) {
+            if (!produce_phase<TO, TRI_NONE>(a.BW, n + m1, m2, a.ldBW, R, g)) break;
+            if (!produce_phase<TO, TRI_NONE>(a.BWT, m2, n + m1, a.ldBWT, R, g)) break;
+        } else {
+            if (!produce_phase<TO, TRI_NONE>(a.CWT, n, m2, a.ldCWT, R, g)) break;
+            if (!produce_phase<TO, TRI_LOWER>(a.WH, n, n, a.ldWH, R, g)) break;
+            if (m1 > 0 && !produce_phase<TO, TRI_NONE>(a.Et, m1, n, a.ldEt, R, g)) break;
+            if (!produce_phase<TO, TRI_UPPER>(a.WHT, n, n, a.ldWHT, R, g)) break;
+            if (m1 > 0 && !produce_phase<TO, TRI_NONE>(a.EtT, n, m1, a.ldEtT, R, g)) break;
+            if (!produce_phase<TO, TRI_NONE>(a.CW, m2, n, a.ldCW, R, g)) break;
+        }
         if (PC == PC_H_K) {
             if (!produce_phase<TP, TRI_LOWER>(a.WPl, m2, m2, a.ldWP, R, g)) break;
             if (!produce_phase<TP, TRI_UPPER>(a.WPu, m2, m2, a.ldWP, R, g)) break;
@@ -615,6 +626,8 @@ __global__ void __launch_bounds__(NT, NT == kSmallBlock ? 2 : 1) pcg_fused_kerne
     const int padO_n = ((n + CHO - 1) / CHO) * CHO, padO_m2 = ((m2 + CHO - 1) / CHO) * CHO;
     const int padO_m1 = ((m1 + CHO - 1) / CHO) * CHO, padP_m2 = ((m2 + CHP - 1) / CHP) * CHP;
     TO* xs2 = xs + padO_n;   // z2, beside z1, for the back solve
+    const int padO_nm1 = ((n + m1 + CHO - 1) / CHO) * CHO;
+    const int qcols = a.wform ? n + m1 : n;   // columns of the matrix whose partials make C y
     const bool stamp = a.tstamp != nullptr && blockIdx.x == 0 && tid == 0;
     auto mark = [&](int it, int ph) {
         if (stamp && it < 4) a.tstamp[it * 32 + ph] = gtimer();
@@ -651,51 +664,68 @@ __global__ void __launch_bounds__(NT, NT == kSmallBlock ? 2 : 1) pcg_fused_kerne
 
     while (true) {
         mark(it, 0);
-        // ---- P1 (a6): u = C' p
-        gemv_ring<TO, TRI_NONE, NT>(R, g, n, m2, a.ldCWT, xs, a.PU, a.ldU, &s_err);
-        mark(it, 11);
-        if (!gsync()) { leave(); return; }
-        mark(it, 1);
-        // ---- P2 (a7, forward solve with L): z1 = R^{-T} u, Et u (z2 = -Et u)
-        stage_sum<NT, TO, TO, TRI_NONE>(xs, a.PU, a.ldU, m2, n, padO_n, [&](int, AT v) { return (TO)v; });
-        csync<NT>();
-        mark(it, 12);
-        gemv_ring<TO, TRI_LOWER, NT>(R, g, n, n, a.ldWH, xs, a.PZ1, a.ldZ1, &s_err);
-        if (m1 > 0) gemv_ring<TO, TRI_NONE, NT>(R, g, m1, n, a.ldEt, xs, a.PZ2, a.ldZ2, &s_err);
-        mark(it, 13);
-        if (!gsync()) { leave(); return; }
-        mark(it, 2);
-        // ---- P3 (a7, back solve with L'): y = R^{-1} z1 + Et' z2
-        stage_sum<NT, TO, TO, TRI_LOWER>(xs, a.PZ1, a.ldZ1, n, n, padO_n, [&](int, AT v) { return (TO)v; });
-        if (m1 > 0)
-            stage_sum<NT, TO, TO, TRI_NONE>(xs2, a.PZ2, a.ldZ2, n, m1, padO_m1, [&](int, AT v) { return (TO)(-v); });
-        csync<NT>();
-        mark(it, 14);
-        gemv_ring<TO, TRI_UPPER, NT>(R, g, n, n, a.ldWHT, xs, a.PY, a.ldY, &s_err);
-        if (m1 > 0) gemv_ring<TO, TRI_NONE, NT>(R, g, n, m1, a.ldEtT, xs2, a.PT, a.ldT, &s_err);
-        mark(it, 15);
-        if (!gsync()) { leave(); return; }
-        mark(it, 5);
-        // ---- P4 (a8): q = D p + C y
-        if (m1 > 0) {
-            stage_sum<NT, TO, TO, TRI_NONE>(xs, a.PT, a.ldT, m1, n, padO_n, [&](int, AT v) { return (TO)v; });
+        if (a.wform) {
+            // ---- W1 (a6-a7): w = B p, B = L^{-1}[C'; 0] (rows R^{-T} C', then Et C')
+            gemv_ring<TO, TRI_NONE, NT>(R, g, n + m1, m2, a.ldBW, xs, a.PW, a.ldPW, &s_err);
+            mark(it, 11);
+            if (!gsync()) { leave(); return; }
+            mark(it, 1);
+            // ---- W2 (a7-a8): C y = B' J w with J = diag(I_n, -I_m1)
+            stage_sum<NT, TO, TO, TRI_NONE>(xs, a.PW, a.ldPW, m2, n + m1, padO_nm1,
+                                            [&](int j, AT v) { return (TO)(j < n ? v : -v); });
             csync<NT>();
-            stage_sum<NT, TO, TO, TRI_UPPER>(xs, a.PY, a.ldY, n, n, padO_n,
-                                         [&](int j, AT v) { return (TO)(v + (AT)xs[j]); });
+            mark(it, 16);
+            gemv_ring<TO, TRI_NONE, NT>(R, g, m2, n + m1, a.ldBWT, xs, a.PQ, a.ldQ, &s_err);
+            mark(it, 17);
+            if (!gsync()) { leave(); return; }
+            mark(it, 6);
         } else {
-            stage_sum<NT, TO, TO, TRI_UPPER>(xs, a.PY, a.ldY, n, n, padO_n, [&](int, AT v) { return (TO)v; });
+            // ---- P1 (a6): u = C' p
+            gemv_ring<TO, TRI_NONE, NT>(R, g, n, m2, a.ldCWT, xs, a.PU, a.ldU, &s_err);
+            mark(it, 11);
+            if (!gsync()) { leave(); return; }
+            mark(it, 1);
+            // ---- P2 (a7, forward solve with L): z1 = R^{-T} u, Et u (z2 = -Et u)
+            stage_sum<NT, TO, TO, TRI_NONE>(xs, a.PU, a.ldU, m2, n, padO_n, [&](int, AT v) { return (TO)v; });
+            csync<NT>();
+            mark(it, 12);
+            gemv_ring<TO, TRI_LOWER, NT>(R, g, n, n, a.ldWH, xs, a.PZ1, a.ldZ1, &s_err);
+            if (m1 > 0) gemv_ring<TO, TRI_NONE, NT>(R, g, m1, n, a.ldEt, xs, a.PZ2, a.ldZ2, &s_err);
+            mark(it, 13);
+            if (!gsync()) { leave(); return; }
+            mark(it, 2);
+            // ---- P3 (a7, back solve with L'): y = R^{-1} z1 + Et' z2
+            stage_sum<NT, TO, TO, TRI_LOWER>(xs, a.PZ1, a.ldZ1, n, n, padO_n, [&](int, AT v) { return (TO)v; });
+            if (m1 > 0)
+                stage_sum<NT, TO, TO, TRI_NONE>(xs2, a.PZ2, a.ldZ2, n, m1, padO_m1, [&](int, AT v) { return (TO)(-v); });
+            csync<NT>();
+            mark(it, 14);
+            gemv_ring<TO, TRI_UPPER, NT>(R, g, n, n, a.ldWHT, xs, a.PY, a.ldY, &s_err);
+            if (m1 > 0) gemv_ring<TO, TRI_NONE, NT>(R, g, n, m1, a.ldEtT, xs2, a.PT, a.ldT, &s_err);
+            mark(it, 15);
+            if (!gsync()) { leave(); return; }
+            mark(it, 5);
+            // ---- P4 (a8): q = D p + C y
+            if (m1 > 0) {
+                stage_sum<NT, TO, TO, TRI_NONE>(xs, a.PT, a.ldT, m1, n, padO_n, [&](int, AT v) { return (TO)v; });
+                csync<NT>();
+                stage_sum<NT, TO, TO, TRI_UPPER>(xs, a.PY, a.ldY, n, n, padO_n,
+                                             [&](int j, AT v) { return (TO)(v + (AT)xs[j]); });
+            } else {
+                stage_sum<NT, TO, TO, TRI_UPPER>(xs, a.PY, a.ldY, n, n, padO_n, [&](int, AT v) { return (TO)v; });
+            }
+            csync<NT>();
+            mark(it, 16);
+            gemv_ring<TO, TRI_NONE, NT>(R, g, m2, n, a.ldCW, xs, a.PQ, a.ldQ, &s_err);
+            mark(it, 17);
+            if (!gsync()) { leave(); return; }
+            mark(it, 6);
         }
-        csync<NT>();
-        mark(it, 16);
-        gemv_ring<TO, TRI_NONE, NT>(R, g, m2, n, a.ldCW, xs, a.PQ, a.ldQ, &s_err);
-        mark(it, 17);
-        if (!gsync()) { leave(); return; }
-        mark(it, 6);
 
         // ---- P5 (a10): q = D p + C y (cached), alpha = r'z / p'q, x += alpha p, r -= alpha q
         // (p'q is summed while q is staged: each thread takes its rows in increasing order)
         AT pq = AT(0);
-        stage_sum_pre<NT, TO, TO, TRI_NONE>(qc, a.PQ, a.ldQ, n, m2, m2, [&](int j) { return __ldg(a.D + j); },
+        stage_sum_pre<NT, TO, TO, TRI_NONE>(qc, a.PQ, a.ldQ, qcols, m2, m2, [&](int j) { return __ldg(a.D + j); },
                                         [&](int j, AT v, TO dj) {
                                             const TO q = (TO)fma((AT)dj, (AT)pcs[j], v);
                                             pq = fma((AT)pcs[j], (AT)q, pq);

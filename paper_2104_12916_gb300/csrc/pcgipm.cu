@@ -80,6 +80,7 @@ void qp_opts_default(qp_opts* o) {
     o->mixed_fallback = 1;
     o->pcg_blocks = 0;
     o->blocking_wait = 0;
+    o->pcg_form = 0;
     o->stream = nullptr;
 }
 
