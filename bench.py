@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--profile-pcg", type=int, default=0, metavar="ITERS",
                     help="only factor the QP and run ITERS PCG iterations (a short run for ncu)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"], help="precision of --profile-pcg")
+    ap.add_argument("--pcg-form", type=int, default=0, choices=[0, 1],
+                    help="--profile-pcg: 0 the implicit K_F product, 1 the W-form")
     ap.add_argument("--workload", default="single", choices=["single", "batch", "serving"],
                     help="batch: the 512 batched QPs through qp_batch_solve; "
                          "serving: a Poisson stream of the served workload's QPs through qp_server_*")
@@ -296,7 +298,15 @@ def run_ours(args):
              "achieved_GBps": round(by_w / (ms_w * 1e-3) / 1e9, 1),
              "frac": round(by_w / (ms_w * 1e-3) / 1e9 / peak, 4),
              "qps_per_s": round((1.0 if ok_w else 0.0) / (ms_wsolve / 1e3), 4), "ms_per_solve": round(ms_wsolve, 1),
-             "ipm_iters": rw[0]["ipm"], "pcg_iters": rw[0]["pcg"], "obj_rel_err": abs(rw[0]["f"] - gold["f"]) / abs(gold["f"])}
+             "ipm_iters": rw[0]["ipm"], "pcg_iters": rw[0]["pcg"], "obj_rel_err": abs(rw[0]["f"] - gold["f"]) / abs(gold["f"]),
+             "traffic": None}
+    try:
+        with open(os.path.join(ROOT, "profiles", "pcg_iteration_traffic_wform.json")) as fh:
+            trw = json.load(fh)
+        if trw.get("source_hash") == source_hash():
+            wform["traffic"] = trw.get("dram_bytes_per_iteration")
+    except Exception:
+        pass
 
     # ---- end to end through host buffers (H2D of the inputs and D2H of x inside)
     e2e_ms = 0.0
@@ -397,13 +407,14 @@ def run_profile(args):
     o = B.qp_opts_default()
     o.precision = B.QP_PREC_FP32 if args.precision == "fp32" else B.QP_PREC_FP64
     o.mixed_fallback = 0          # time the FP32 kernels themselves
+    o.pcg_form = args.pcg_form
     h = B.qp_create(qp.H, qp.c, qp.A, qp.b, np.ascontiguousarray(qp.C), qp.d, o)
     B.qp_factor_K0(h)
     Dmid = np.exp(np.random.default_rng(7).uniform(np.log(1e-1), np.log(1e1), qp.m2))
     ms = B.qp_time_pcg_iteration(h, Dmid, precond=B.QP_PC_AUTO, warmup=8, iters=args.profile_pcg)
     by = B.qp_pcg_bytes_per_iter(h, B.QP_PC_AUTO)
     print(json.dumps({"pcg_iteration_us": ms * 1e3, "algorithmic_MB": by / 1e6,
-                      "GBps": by / (ms * 1e-3) / 1e9, "precision": args.precision}))
+                      "GBps": by / (ms * 1e-3) / 1e9, "precision": args.precision, "pcg_form": args.pcg_form}))
     B.qp_destroy(h)
 
 
