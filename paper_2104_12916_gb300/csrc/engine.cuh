@@ -206,6 +206,7 @@ public:
     size_t cl_smem = 0;
     bool cl_ok = false;
     bool phase_times = false;
+    bool leave_early = false;   // PCGIPM_TEST_LEAVE_EARLY=1: failure-detection test of the bounded waits
     unsigned long long* tstamp = nullptr;
 
     // FP64 IPM vectors
@@ -244,6 +245,8 @@ public:
         verbose = v && v[0] == '1';
         const char* pt = std::getenv("PCGIPM_PHASE_TIMES");
         phase_times = pt && pt[0] == '1';
+        const char* le = std::getenv("PCGIPM_TEST_LEAVE_EARLY");
+        leave_early = le && le[0] == '1';
         allow_pc64 = opt.mixed_fallback != 0;
     }
 
@@ -858,6 +861,7 @@ public:
         fa.ldV = P.ldV; fa.ldZ = P.ldV;
         fa.st = st; fa.bar = bar;
         fa.tstamp = phase_times ? tstamp : nullptr;
+        fa.leave_early = leave_early ? 1 : 0;
         auto kern = pcg_fused_kernel<TO, TP, PC, NT>;
         const size_t xsb = fused_xs_bytes<TO, TP>();
         fa.xs_bytes = xsb;

@@ -526,6 +526,7 @@ struct FusedArgs {
     size_t ring_off;   // byte offset of the slot ring (128-byte aligned)
     int slots;         // ring depth S
     unsigned long long* tstamp;   // optional: %globaltimer at phase marks of the first 4 iterations
+    int leave_early;              // failure-detection test: block 0 leaves before its first grid barrier
 };
 
 // Shared-memory layout of the persistent kernel: staged vector, three m2-vector
@@ -661,6 +662,10 @@ __global__ void __launch_bounds__(NT, NT == kSmallBlock ? 2 : 1) pcg_fused_kerne
     csync<NT>();
     for (int j = tid; j < padO_m2; j += kFusedThreads) xs[j] = (j < m2) ? pcs[j] : TO(0);
     csync<NT>();
+
+    // failure-detection test: block 0 stops before the first grid barrier, as a block
+    // that died would; every other block's bounded wait runs out and reports QP_ETIMEOUT
+    if (a.leave_early && blockIdx.x == 0 && nblocks > 1) { leave(); return; }
 
     while (true) {
         mark(it, 0);
