@@ -44,7 +44,7 @@ def parse():
                     help="only factor the QP and run ITERS PCG iterations (a short run for ncu)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"], help="precision of --profile-pcg")
     ap.add_argument("--pcg-form", type=int, default=0, choices=[0, 1],
-                    help="--profile-pcg: 0 the implicit K_F product, 1 the W-form")
+                    help="--profile-pcg, batch, serving: 0 the implicit K_F product, 1 the W-form")
     ap.add_argument("--workload", default="single", choices=["single", "batch", "serving"],
                     help="batch: the 512 batched QPs through qp_batch_solve; "
                          "serving: a Poisson stream of the served workload's QPs through qp_server_*")
@@ -439,7 +439,7 @@ def run_batch(args):
     out = {}
     for prec in (B.QP_PREC_FP32, B.QP_PREC_FP64):
         o = B.qp_opts_default()
-        o.precision, o.blocking_wait = prec, 1
+        o.precision, o.blocking_wait, o.pcg_form = prec, 1, args.pcg_form
         l0 = B.qp_kernel_launches()
         with ClockSampler(local) as clk:
             t0 = time.perf_counter()
@@ -473,7 +473,8 @@ def run_batch(args):
             "ms_per_step": round(m["solve_s"] * 1e3, 1), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": BATCH_WORKLOAD, "qps": len(qps), "in_flight": args.concurrency,
-                       "precision": "mixed (FP32 operator and P_H, FP64 refinement)"},
+                       "precision": "mixed (FP32 operator and P_H, FP64 refinement)",
+                       "pcg_form": "W-form" if args.pcg_form else "implicit"},
             "solved": f"{sum(m['ok'])}/{len(qps)}",
             "fp64": {"value": round(sum(m64["ok"]) / m64["solve_s"], 3), "unit": "QPs/s",
                      "solved": f"{sum(m64['ok'])}/{len(qps)}"},
@@ -507,7 +508,7 @@ def run_serving(args):
     qps = [qpgen.serving_qp(i) for i in idx]
     arrive = qpgen.arrival_times(len(qps), args.rate)
     o = B.qp_opts_default()
-    o.blocking_wait = 1
+    o.blocking_wait, o.pcg_form = 1, args.pcg_form
     srv = B.Server(budget_bytes=int(args.budget_gb * 1e9), max_slots=args.slots, opts=o)
     l0 = B.qp_kernel_launches()
     results = {}
