@@ -547,7 +547,8 @@ def run_serving(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": SERVING_WORKLOAD, "rate_per_s": args.rate, "requests": len(qps),
                        "max_n": args.max_n, "budget_gb": args.budget_gb, "slots": args.slots,
-                       "precision": "mixed (FP32 operator and P_H, FP64 refinement)"},
+                       "precision": "mixed (FP32 operator and P_H, FP64 refinement)",
+                       "pcg_form": "W-form" if args.pcg_form else "implicit"},
             "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 1), "p99": round(float(np.percentile(lat, 99)), 1),
                            "max": round(float(lat.max()), 1)},
             "wait_ms_p50": round(float(np.percentile([results[i][0]["wait_ms"] for i in range(len(qps))], 50)), 1),
