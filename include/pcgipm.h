@@ -306,11 +306,16 @@ int qp_time_pcg_iteration(qp_t qp, const double *D, int precond, int warmup, int
  * q = D o p + C y.  Requires 1 <= n <= QP_STATIC_MAX_N, 0 <= m1 <= n, m2 >= 1
  * (QP_EINVAL otherwise).  It calls no cudaMalloc/cudaFree and no allocating
  * library routine: the intermediate vectors live in one file-scope device array
- * that every device which loads the library holds until the process exits.
- * The first call on a device looks up that array's device address
- * (cudaGetSymbolAddress, with the device current); make that first call before
- * any stream capture.  The work is enqueued on `stream` (a cudaStream_t cast to
- * void*, NULL = the default stream) and the call returns without waiting.  All
+ * that every device which uses the library's module holds until the process
+ * exits (under lazy module loading, the default since CUDA 12.2, the array is
+ * reserved when the module is first used on a device, not when the library is
+ * loaded).  The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress, with the device current), which may load the module;
+ * make that first call before any stream capture.  The work is enqueued on
+ * `stream` (a cudaStream_t cast to void*, NULL = the default stream) and the
+ * call returns without waiting.  QP_ECUDA: an error was already pending when
+ * the call began (it is left in place), or a launch failed; an error during
+ * execution shows at the caller's next synchronisation with the stream.  All
  * calls on a device share the array: calls that overlap on the GPU (different
  * streams, or different host threads) race on it and must be serialised by the
  * caller.  Every intermediate is written before it is read, so nothing left by

@@ -135,16 +135,3 @@ def pcg(apply_K, apply_Minv, rhs, tol, maxit):
         p = z + beta * p
     return x, it, hist
 
-
-def augmented_matrix(H, A, C, D):
-    """K^{(k)} = [-H A' C'; A 0 0; C 0 D], Sec. 2.1, eq. [augmented]."""
-    n, m1, m2 = H.shape[0], A.shape[0], C.shape[0]
-    N = n + m1 + m2
-    K = np.zeros((N, N))
-    K[:n, :n] = -H
-    K[:n, n:n + m1] = A.T
-    K[:n, n + m1:] = C.T
-    K[n:n + m1, :n] = A
-    K[n + m1:, :n] = C
-    K[n + m1:, n + m1:] = np.diag(D)
-    return K

@@ -299,13 +299,35 @@ def qp_time_pcg_iteration(h, D, precond=QP_PC_AUTO, warmup=8, iters=64) -> float
 def qp_kf_apply_static(C, WH, Gt, D, p, q, stream=None):
     """q = K_F p through the no-allocation entry point (all torch CUDA float64
     tensors; Gt may be None when m1 = 0).  Enqueued on `stream` (a torch stream
-    or None for the default stream); returns the status."""
+    or None for the default stream); returns the status.
+
+    The C side receives raw pointers and cannot check sizes, so every shape and
+    device is checked here before the call: C (m2, n), WH (n, n), Gt (m1, n),
+    D, p, q (m2,), all on one CUDA device that is the current device and the
+    stream's device."""
+    if C.dim() != 2:
+        raise ValueError("C must be a matrix (m2, n)")
     m2, n = int(C.shape[0]), int(C.shape[1])
     m1 = 0 if Gt is None else int(Gt.shape[0])
+    if tuple(WH.shape) != (n, n):
+        raise ValueError(f"WH must be ({n}, {n}), got {tuple(WH.shape)}")
+    if Gt is not None and (Gt.dim() != 2 or int(Gt.shape[1]) != n):
+        raise ValueError(f"Gt must be (m1, {n}), got {tuple(Gt.shape)}")
+    for name, v in (("D", D), ("p", p), ("q", q)):
+        if v.dim() != 1 or int(v.shape[0]) != m2:
+            raise ValueError(f"{name} must be ({m2},), got {tuple(v.shape)}")
+    tensors = [a for a in (C, WH, Gt, D, p, q) if a is not None]
+    if not all(a.is_cuda for a in tensors):
+        raise TypeError("qp_kf_apply_static takes CUDA tensors")
+    import torch
+    devs = {a.device.index for a in tensors}
+    cur = torch.cuda.current_device()
+    if devs != {cur}:
+        raise ValueError(f"all tensors must be on the current device cuda:{cur}, got {sorted(devs)}")
+    if stream is not None and stream.device.index != cur:
+        raise ValueError(f"stream is on cuda:{stream.device.index}, the tensors on cuda:{cur}")
     kh = [None]
     args = [_ptr(C, kh), _ptr(WH, kh), _ptr(Gt, kh), _ptr(D, kh), _ptr(p, kh), _ptr(q, kh)]
-    if kh[0] != QP_PTR_DEVICE:
-        raise TypeError("qp_kf_apply_static takes device tensors")
     sp = None if stream is None else stream.cuda_stream
     return _check(load().qp_kf_apply_static(n, m1, m2, *args, sp), "qp_kf_apply_static")
 

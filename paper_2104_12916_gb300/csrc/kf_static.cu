@@ -5,8 +5,10 @@
 // under an allocator it does not own, inside a region where cudaMalloc would
 // synchronise the device or is forbidden, or on a memory budget fixed in
 // advance).  The caller passes every input and the output; the intermediate
-// vectors live in the file-scope array below, reserved once in every device's
-// memory when the library is loaded and kept until the process exits.
+// vectors live in the file-scope array below.  Under CUDA's lazy module loading
+// (the default since CUDA 12.2) the array is reserved in a device's memory when
+// this module is first used on that device -- at the first cudaGetSymbolAddress
+// or launch -- and kept until the process exits.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -90,6 +92,9 @@ extern "C" int qp_kf_apply_static(int n, int m1, int m2, const double* C, const 
                                   const double* D, const double* p, double* q, void* stream) {
     if (n < 1 || n > kStaticMaxN || m1 < 0 || m1 > n || m2 < 1) return QP_EINVAL;
     if (!C || !WH || !D || !p || !q || (m1 > 0 && !Gt)) return QP_EINVAL;
+    // An error left pending by an earlier, unrelated call is reported (and left in
+    // place for its owner) instead of being mistaken for one of this call's launches.
+    if (cudaPeekAtLastError() != cudaSuccess) return QP_ECUDA;
     double* scratch = nullptr;
     if (scratch_for_current_device(&scratch) != cudaSuccess) {
         cudaGetLastError();
@@ -119,6 +124,8 @@ extern "C" int qp_kf_apply_static(int n, int m1, int m2, const double* C, const 
     col_gemv<<<cols_grid(n), T, 0, s>>>(WH, n, n, 1, top, 1.0, nullptr, 0.0, y);
     // q = D p + C y
     row_gemv<<<rows_grid(m2), T, 0, s>>>(C, m2, n, 0, y, 1.0, nullptr, 0.0, D, p, q);
+    // launch errors only: an error during execution shows at the caller's next
+    // synchronisation with the stream
     if (cudaGetLastError() != cudaSuccess) return QP_ECUDA;
     return QP_OK;
 }

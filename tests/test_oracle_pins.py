@@ -278,3 +278,42 @@ def test_pins_catch_the_garbled_r_a():
     K = reduced.kf_explicit(q.H, q.A, q.C, D)
     dnu_bad = np.linalg.solve(K, reduced.r_nu(q.H, q.A, q.C, r_g, r_e, r_i - D * r_c))
     assert np.linalg.norm(dnu_bad - full[2]) > 1e-3 * np.linalg.norm(full[2])
+
+
+# ------------------------------------- P_H with diag(H)^{-1} (the experiments' variant)
+def test_PH_diag_variant_equals_exact_for_diagonal_H():
+    """With a diagonal H, diag(H)^{-1} = H^{-1}, so the variant of Sec. 5.2 (PH-KF)
+    coincides with the P_H of eq. [preconditioner-2]."""
+    rng = np.random.default_rng(5)
+    h = rng.uniform(0.3, 7.0, 9)
+    C = rng.standard_normal((13, 9))
+    D = rng.uniform(0.1, 2.0, 13)
+    exact = reduced.P_H(np.diag(h), C, D, exact=True)
+    diag = reduced.P_H(np.diag(h), C, D, exact=False)
+    assert np.allclose(diag, exact, rtol=1e-13, atol=1e-13)
+
+
+def test_PH_diag_variant_hand_computed():
+    """A case worked by hand.  H = [[2,1,0],[1,4,1],[0,1,5]] (its off-diagonal
+    entries must be ignored), C = [[1,0,2],[0,1,-1]], D = (0.5, 0.25):
+      C diag(H)^{-1} C' = [[1/2 + 4/5, -2/5], [-2/5, 1/4 + 1/5]] = [[1.3, -0.4], [-0.4, 0.45]],
+      P_H(diag) = D + that = [[1.8, -0.4], [-0.4, 0.7]].
+    The exact P_H differs: det(H) = 33, adj(H) = [[19,-5,1],[-5,10,-2],[1,-2,7]], so
+      C H^{-1} C' = (1/33) [[51, -24], [-24, 21]],
+      P_H(exact) = [[0.5 + 51/33, -24/33], [-24/33, 0.25 + 21/33]]."""
+    H = np.array([[2.0, 1.0, 0.0], [1.0, 4.0, 1.0], [0.0, 1.0, 5.0]])
+    C = np.array([[1.0, 0.0, 2.0], [0.0, 1.0, -1.0]])
+    D = np.array([0.5, 0.25])
+    assert np.allclose(reduced.P_H(H, C, D, exact=False), [[1.8, -0.4], [-0.4, 0.7]], rtol=0, atol=1e-15)
+    want = np.array([[0.5 + 51 / 33, -24 / 33], [-24 / 33, 0.25 + 21 / 33]])
+    assert np.allclose(reduced.P_H(H, C, D, exact=True), want, rtol=0, atol=1e-14)
+
+
+def test_pins_catch_diag_H_instead_of_its_inverse():
+    """A planted slip, C diag(H) C' in place of C diag(H)^{-1} C', misses the
+    hand-computed values above (so that pin can fail)."""
+    H = np.array([[2.0, 1.0, 0.0], [1.0, 4.0, 1.0], [0.0, 1.0, 5.0]])
+    C = np.array([[1.0, 0.0, 2.0], [0.0, 1.0, -1.0]])
+    D = np.array([0.5, 0.25])
+    bad = np.diag(D) + (C * np.diag(H)[None, :]) @ C.T
+    assert not np.allclose(bad, [[1.8, -0.4], [-0.4, 0.7]], rtol=0, atol=1e-3)
