@@ -1,6 +1,7 @@
 #!/usr/bin/env python3
-"""Benchmark: QPs solved per second on the dense few-equalities QP
-(n=2000, m_eq=200, m_in=4000, seed 1), mixed precision vs plain FP64.
+"""Benchmark: QPs solved per second on the dense few-degrees-of-freedom QP
+(n=3000, m_eq=2600, m_in=6000, seed 2), mixed precision vs plain FP64; the
+few-equalities QP (n=2000, m_eq=200, m_in=4000, seed 1) alongside.
 
 A step is one whole solve through the C ABI: qp_create from inputs resident in
 HBM (device-to-device copy), qp_factor_K0 (the setup phase), qp_ipm_solve (all
@@ -28,9 +29,14 @@ sys.path.insert(0, ROOT)
 
 import qpgen  # noqa: E402
 
-WORKLOAD = "dense convex QP n=2000 m_eq=200 m_in=4000 (Lambda log-uniform [1e-3,1e3], seed 1)"
+WORKLOADS = {
+    2: "dense convex QP n=3000 m_eq=2600 m_in=6000, few degrees of freedom (A rows orthogonal, "
+       "scaled log-uniform [1e-2,1]; Lambda log-uniform [1e-2,1e2], seed 2)",
+    1: "dense convex QP n=2000 m_eq=200 m_in=4000, few equalities (Lambda log-uniform [1e-3,1e3], seed 1)",
+}
 METRIC = "QPs solved/s at 1e-6 obj err (mixed precision; FP64 path alongside)"
-CONFIG_ID = 1
+HEADLINE = 2
+FORM_NAMES = {0: "C', M0 = [K0^-1]_11, C", 1: "B = L^-1[C'; 0] and B'", 2: "C', forward and back solve, C"}
 
 
 def parse():
@@ -39,11 +45,17 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--fp64-steps", type=int, default=1, help="timed steps of the FP64 comparison line")
+    ap.add_argument("--fp64-steps", type=int, default=3, help="timed steps of the FP64 comparison line (at least 3)")
+    ap.add_argument("--config", type=int, default=HEADLINE, choices=[1, 2], help="workload of value (1 or 2)")
+    ap.add_argument("--no-extras", action="store_true", help="skip the other workload, batch and serving keys")
+    ap.add_argument("--extra-batch", type=int, default=64, help="QPs of the batch key")
+    ap.add_argument("--extra-requests", type=int, default=48, help="requests of the serving key")
+    ap.add_argument("--extra-rate", type=float, default=200.0, help="arrival rate of the serving key")
+    ap.add_argument("--extra-max-n", type=int, default=2048, help="largest n of the serving key")
     ap.add_argument("--profile-pcg", type=int, default=0, metavar="ITERS",
                     help="only factor the QP and run ITERS PCG iterations (a short run for ncu)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"], help="precision of --profile-pcg")
-    ap.add_argument("--pcg-form", type=int, default=0, choices=[0, 1],
+    ap.add_argument("--pcg-form", type=int, default=0, choices=[0, 1, 2],
                     help="--profile-pcg, batch, serving: 0 the implicit K_F product, 1 the W-form")
     ap.add_argument("--workload", default="single", choices=["single", "batch", "serving"],
                     help="batch: the 512 batched QPs through qp_batch_solve; "
@@ -52,14 +64,15 @@ def parse():
     ap.add_argument("--concurrency", type=int, default=16, help="batch: QPs in flight")
     ap.add_argument("--requests", type=int, default=64, help="serving: number of requests")
     ap.add_argument("--rate", type=float, default=50.0, help="serving: arrival rate (requests/s)")
+    ap.add_argument("--rates", default="", help="serving: comma-separated arrival rates to sweep")
     ap.add_argument("--budget-gb", type=float, default=150.0, help="serving: HBM admission budget")
     ap.add_argument("--slots", type=int, default=64, help="serving: QPs in flight at most")
     ap.add_argument("--max-n", type=int, default=4096, help="serving: skip requests with n above this")
     return ap.parse_args()
 
 
-def golden():
-    with open(os.path.join(ROOT, "tests", "golden", f"oracle_config{CONFIG_ID}.json")) as fh:
+def golden(cfg):
+    with open(os.path.join(ROOT, "tests", "golden", f"oracle_config{cfg}.json")) as fh:
         return json.load(fh)
 
 
@@ -85,24 +98,25 @@ def reduce_over_ranks(total_ms, solved, device=None):
 
 
 # ---------------------------------------------------------------- CPU baseline
-def oracle_sample(qp, ipm_iters_full, sample_iters=2):
+def oracle_sample(qp, ipm_iters_full, sample_iters=1):
     """Time the FP64 oracle (3x3 LDL^T variant) on a bounded sample of the same
-    workload: its setup plus `sample_iters` IPM iterations, scaled to a full solve
-    by the oracle's own iteration count."""
+    workload: its start point plus `sample_iters` IPM iterations, scaled to a full
+    solve by the oracle's own iteration count.  Returns the baseline dict and the
+    seconds the sample took."""
     from oracle import ipm
     t0 = time.perf_counter()
     ipm.start_point(qp.H, qp.c, qp.A, qp.b, qp.C, qp.d)
     t_setup = time.perf_counter() - t0
-    t0 = time.perf_counter()
+    t1 = time.perf_counter()
     ipm.solve_qp(qp, variant="kkt3", max_ipm=sample_iters)
-    t_iters = time.perf_counter() - t0 - t_setup
-    per_iter = t_iters / sample_iters
+    t_run = time.perf_counter() - t1
+    per_iter = max(t_run - t_setup, 1e-9) / sample_iters
     t_full = t_setup + per_iter * ipm_iters_full
     cores = len(os.sched_getaffinity(0))
     return dict(value=1.0 / t_full, unit="QPs/s", cores=cores, kind="oracle",
                 sample=f"start point + {sample_iters} of {ipm_iters_full} IPM iterations of the FP64 "
                        f"3x3-LDL^T oracle on the same QP, scaled to the full solve "
-                       f"({per_iter:.2f} s/iteration, {t_full:.1f} s/QP)")
+                       f"({per_iter:.2f} s/iteration, {t_full:.1f} s/QP)"), t_setup + t_run
 
 
 # ---------------------------------------------------------------------- clocks
@@ -160,6 +174,69 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ our solver
+STAT_KEYS = ("newton_solves", "refine_sweeps", "op64_switch_iter", "pc64_switch_iter", "pc_switch_iter",
+             "op64_solves", "t_factor_ms", "t_pcg_ms", "t_precond_ms", "t_solve_ms")
+
+
+def per_solve(r):
+    """Counters of one solve: Newton directions, refinement sweeps, PCG iterations
+    per Newton direction, and where the mixed path moved to FP64 (-1: never)."""
+    st = r["stats"]
+    d = {k: (round(st[k], 1) if isinstance(st[k], float) else st[k]) for k in STAT_KEYS}
+    d["pcg_iters"] = r["pcg"]
+    d["pcg_per_newton"] = round(r["pcg"] / max(1, st["newton_solves"]), 1)
+    return d
+
+
+class Solver:
+    """One workload resident on the device, solved through the C ABI."""
+
+    def __init__(self, B, cfg, dev, stream):
+        import torch
+        self.B, self.cfg, self.dev, self.stream = B, cfg, dev, stream
+        self.qp = qpgen.config_qp(cfg)
+        self.gold = golden(cfg)
+        t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+        q = self.qp
+        self.args = (t(q.H), t(q.c), t(q.A), t(q.b), t(q.C), t(q.d))
+        self.x = torch.zeros(q.n, dtype=torch.float64, device=dev)
+
+    def opts(self, prec, form=0):
+        o = self.B.qp_opts_default()
+        o.precision = prec
+        o.pcg_form = form
+        o.stream = self.stream.cuda_stream
+        return o
+
+    def ok(self, r):
+        return r["status"] == 0 and abs(r["f"] - self.gold["f"]) / max(abs(self.gold["f"]), 1.0) <= 1e-6
+
+    def step(self, prec, out, form=0):
+        B = self.B
+        h = B.qp_create(*self.args, self.opts(prec, form))
+        try:
+            st, f, its, pits = B.qp_ipm_solve(h, self.x, allow=(B.QP_OK, B.QP_EMAXIT, B.QP_ENUMERIC))
+            out.append(dict(status=st, f=f, ipm=its, pcg=pits, stats=B.qp_get_stats(h)))
+        finally:
+            B.qp_destroy(h)
+
+    def pcg_iteration(self, prec, form, iters=128):
+        """Mean CUDA-event time of one PCG iteration of the persistent kernel (an
+        early-IPM D of order one, tolerance 0) and its algorithmic bytes."""
+        B = self.B
+        o = self.opts(prec, form)
+        o.mixed_fallback = 0          # the FP32 kernels themselves
+        h = B.qp_create(*self.args, o)
+        try:
+            B.qp_factor_K0(h)
+            D = np.exp(np.random.default_rng(7).uniform(np.log(1e-1), np.log(1e1), self.qp.m2))
+            ms = B.qp_time_pcg_iteration(h, D, precond=B.QP_PC_AUTO, warmup=16, iters=iters)
+            by = B.qp_pcg_bytes_per_iter(h, B.QP_PC_AUTO)
+        finally:
+            B.qp_destroy(h)
+        return ms, by
+
+
 def run_ours(args):
     import torch
     world, rank, local = dist_env()
@@ -170,32 +247,13 @@ def run_ours(args):
     from paper_2104_12916_gb300 import binding as B, build
     build.build()
     B.load()
-    gold = golden()
-    qp = qpgen.config_qp(CONFIG_ID)
     dev = torch.device("cuda", local)
-    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
-    Hd, cd, Ad, bd, Cd, dd = t(qp.H), t(qp.c), t(qp.A), t(qp.b), t(qp.C), t(qp.d)
-    xd = torch.zeros(qp.n, dtype=torch.float64, device=dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > 129 MB L2
-    # The solver runs on this (non-default) stream: PCG graphs are captured on it and
-    # the CUDA events below are recorded on it.
+    # The solver runs on this (non-default) stream: the CUDA events below are recorded on it.
     stream = torch.cuda.Stream(device=dev)
     torch.cuda.synchronize()
     torch.cuda.set_stream(stream)
-
-    def opts(prec):
-        o = B.qp_opts_default()
-        o.precision = prec
-        o.stream = stream.cuda_stream
-        return o
-
-    def step(prec, out):
-        h = B.qp_create(Hd, cd, Ad, bd, Cd, dd, opts(prec))
-        try:
-            st, f, its, pits = B.qp_ipm_solve(h, xd, allow=(B.QP_OK, B.QP_EMAXIT, B.QP_ENUMERIC))
-            out.append(dict(status=st, f=f, ipm=its, pcg=pits, stats=B.qp_get_stats(h)))
-        finally:
-            B.qp_destroy(h)
+    main = Solver(B, args.config, dev, stream)
 
     def barrier():
         if world > 1:
@@ -203,10 +261,10 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def timed(prec, steps, warmup):
+    def timed(sv, prec, steps, warmup, form=0):
         res = []
         for _ in range(warmup):
-            step(prec, [])
+            sv.step(prec, [], form)
         barrier()
         total_ms = 0.0
         l0 = B.qp_kernel_launches()
@@ -214,34 +272,24 @@ def run_ours(args):
             flush.fill_(1.0)                     # evict L2 between timed steps (not timed)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            step(prec, res)
+            sv.step(prec, res, form)
             e1.record(stream)
             e1.synchronize()
             total_ms += e0.elapsed_time(e1)
         barrier()
         launches = B.qp_kernel_launches() - l0
-        ok = [abs(r["f"] - gold["f"]) / max(abs(gold["f"]), 1.0) <= 1e-6 and r["status"] == 0 for r in res]
+        ok = [sv.ok(r) for r in res]
         total_ms, solved_all = reduce_over_ranks(total_ms, sum(ok), dev)
         return res, total_ms, ok, launches, solved_all
 
     with ClockSampler(local) as clk:
-        res, total_ms, ok, launches, solved = timed(B.QP_PREC_FP32, args.steps, args.warmup)
-    res64, total64, ok64, _, solved64 = timed(B.QP_PREC_FP64, args.fp64_steps, 1)
-
+        res, total_ms, ok, launches, solved = timed(main, B.QP_PREC_FP32, args.steps, args.warmup)
+    fp64_steps = max(3, args.fp64_steps)
+    res64, total64, ok64, _, solved64 = timed(main, B.QP_PREC_FP64, fp64_steps, 1)
     value = solved / (total_ms / 1e3)
     value64 = solved64 / (total64 / 1e3)
+    gold = main.gold
 
-    # ---- roofline of the dominant kernel chain: one PCG iteration (a6-a10)
-    o = opts(B.QP_PREC_FP32)
-    o.mixed_fallback = 0          # the FP32 hot path itself (the mixed solve's first phase)
-    h = B.qp_create(Hd, cd, Ad, bd, Cd, dd, o)
-    B.qp_factor_K0(h)
-    # an early-IPM D (s, nu of order one): the FP32 P_H factor applies, so this times
-    # the FP32 hot path (the bytes and work per iteration do not depend on D's values)
-    Dmid = np.exp(np.random.default_rng(7).uniform(np.log(1e-1), np.log(1e1), qp.m2))
-    ms_it = B.qp_time_pcg_iteration(h, Dmid, precond=B.QP_PC_AUTO, warmup=16, iters=128)
-    by_it = B.qp_pcg_bytes_per_iter(h, B.QP_PC_AUTO)
-    B.qp_destroy(h)
     peaks = {}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -249,67 +297,35 @@ def run_ours(args):
     except Exception:
         pass
     peak = peaks.get("hbm_gbs", 6800.0)
-    achieved = by_it / (ms_it * 1e-3) / 1e9
+
+    # ---- the dominant kernel: one PCG iteration (a6-a10) of the persistent kernel, per form
+    def iteration_entry(sv, form):
+        ms, by = sv.pcg_iteration(B.QP_PREC_FP32, form)
+        gbs = by / (ms * 1e-3) / 1e9
+        return {"form": FORM_NAMES[form], "us": round(ms * 1e3, 2), "algorithmic_MB": round(by / 1e6, 2),
+                "GBps": round(gbs, 1), "frac": round(gbs / peak, 4)}
+
+    pcg_it = {f"config{main.cfg}_form{f}": iteration_entry(main, f) for f in (0, 2, 1)}
+    head = pcg_it[f"config{main.cfg}_form0"]
     traffic = None
     try:
-        with open(os.path.join(ROOT, "profiles", "pcg_iteration_traffic.json")) as fh:
+        with open(os.path.join(ROOT, "profiles", f"pcg_iteration_traffic_config{main.cfg}.json")) as fh:
             tr = json.load(fh)
-        from paper_2104_12916_gb300 import build as _b
         if tr.get("source_hash") == source_hash():
             traffic = tr.get("dram_bytes_per_iteration")
     except Exception:
         pass
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": traffic,
-                "kernel": "one PCG iteration on K_F (C'p, K0 solve, C y + D p, update, P_H solve): "
-                          f"{by_it / 1e6:.1f} MB algorithmic, {ms_it * 1e3:.1f} us",
+    pc_name = "P_L (few degrees of freedom)" if main.qp.m1 * 2 >= main.qp.n else "P_H (few equalities)"
+    roofline = {"bound": "hbm", "achieved": head["GBps"], "peak": peak, "unit": "GB/s", "frac": head["frac"],
+                "traffic": traffic,
+                "kernel": f"one PCG iteration on K_F, {pc_name}: C'p, M0 u, C y + D p, update"
+                          + (", P_H^-1 r" if main.qp.m1 * 2 < main.qp.n else "")
+                          + f": {head['algorithmic_MB']} MB algorithmic, {head['us']} us",
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback"}
-
-    # ---- the same path with pcg_form = 1 (K_F through B = L^-1[C'; 0], two matrix phases)
-    o = opts(B.QP_PREC_FP32)
-    o.mixed_fallback, o.pcg_form = 0, 1
-    h = B.qp_create(Hd, cd, Ad, bd, Cd, dd, o)
-    B.qp_factor_K0(h)
-    ms_w = B.qp_time_pcg_iteration(h, Dmid, precond=B.QP_PC_AUTO, warmup=16, iters=128)
-    by_w = B.qp_pcg_bytes_per_iter(h, B.QP_PC_AUTO)
-    B.qp_destroy(h)
-    def step_w(out):
-        ow = opts(B.QP_PREC_FP32)
-        ow.pcg_form = 1
-        hw = B.qp_create(Hd, cd, Ad, bd, Cd, dd, ow)
-        try:
-            st_, f_, its_, pits_ = B.qp_ipm_solve(hw, xd, allow=(B.QP_OK, B.QP_EMAXIT, B.QP_ENUMERIC))
-            out.append(dict(status=st_, f=f_, ipm=its_, pcg=pits_))
-        finally:
-            B.qp_destroy(hw)
-    step_w([])
-    torch.cuda.synchronize()
-    flush.fill_(1.0)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    rw = []
-    e0.record(stream)
-    step_w(rw)
-    e1.record(stream)
-    e1.synchronize()
-    ms_wsolve = e0.elapsed_time(e1)
-    ok_w = abs(rw[0]["f"] - gold["f"]) / max(abs(gold["f"]), 1.0) <= 1e-6 and rw[0]["status"] == 0
-    wform = {"what": "pcg_form=1: K_F p = D p + B1'(B1 p) - B2'(B2 p), B = L^-1[C'; 0] formed once per QP",
-             "pcg_iteration_us": round(ms_w * 1e3, 1), "algorithmic_MB": round(by_w / 1e6, 1),
-             "achieved_GBps": round(by_w / (ms_w * 1e-3) / 1e9, 1),
-             "frac": round(by_w / (ms_w * 1e-3) / 1e9 / peak, 4),
-             "qps_per_s": round((1.0 if ok_w else 0.0) / (ms_wsolve / 1e3), 4), "ms_per_solve": round(ms_wsolve, 1),
-             "ipm_iters": rw[0]["ipm"], "pcg_iters": rw[0]["pcg"], "obj_rel_err": abs(rw[0]["f"] - gold["f"]) / abs(gold["f"]),
-             "traffic": None}
-    try:
-        with open(os.path.join(ROOT, "profiles", "pcg_iteration_traffic_wform.json")) as fh:
-            trw = json.load(fh)
-        if trw.get("source_hash") == source_hash():
-            wform["traffic"] = trw.get("dram_bytes_per_iteration")
-    except Exception:
-        pass
 
     # ---- end to end through host buffers (H2D of the inputs and D2H of x inside)
     e2e_ms = 0.0
+    qp = main.qp
     xh = np.zeros(qp.n)
     Cdense = np.ascontiguousarray(qp.C)
     nsteps_e2e = max(1, min(args.steps, 2))
@@ -319,7 +335,8 @@ def run_ours(args):
         t0 = time.perf_counter()
         o = B.qp_opts_default()
         o.precision = B.QP_PREC_FP32
-        hh = B.qp_create(qp.H, qp.c, qp.A, qp.b, Cdense, qp.d, o)
+        cc = np.ascontiguousarray
+        hh = B.qp_create(cc(qp.H), cc(qp.c), cc(qp.A), cc(qp.b), Cdense, cc(qp.d), o)
         st, f, its, pits = B.qp_ipm_solve(hh, xh, allow=(B.QP_OK, B.QP_EMAXIT, B.QP_ENUMERIC))
         B.qp_destroy(hh)
         e2e_ms += (time.perf_counter() - t0) * 1e3
@@ -330,27 +347,58 @@ def run_ours(args):
     e2e = {"value": e2e_solved / (e2e_ms / 1e3), "unit": "QPs/s", "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h}
 
+    # ---- the other single-QP workload, the batch and the served stream (bounded, rank 0)
+    extras = {}
+    if rank == 0 and not args.no_extras:
+        other = Solver(B, 3 - main.cfg, dev, stream)
+        r1, t1, ok1, _, _ = timed(other, B.QP_PREC_FP32, 2, 1)
+        r1d, t1d, ok1d, _, _ = timed(other, B.QP_PREC_FP64, 2, 0)
+        extras[f"config{other.cfg}"] = {
+            "workload": WORKLOADS[other.cfg],
+            "mixed": {"value": round(sum(ok1) / (t1 / 1e3), 4), "unit": "QPs/s", "ms_per_step": round(t1 / 2, 1),
+                      "solved": f"{sum(ok1)}/{len(ok1)}", "ipm_iters": [r["ipm"] for r in r1],
+                      "oracle_ipm_iters": other.gold["ipm_iters"],
+                      "obj_rel_err": [abs(r["f"] - other.gold["f"]) / abs(other.gold["f"]) for r in r1],
+                      "per_solve": per_solve(r1[-1])},
+            "fp64": {"value": round(sum(ok1d) / (t1d / 1e3), 4), "unit": "QPs/s", "ms_per_step": round(t1d / 2, 1),
+                     "solved": f"{sum(ok1d)}/{len(ok1d)}", "ipm_iters": [r["ipm"] for r in r1d],
+                     "per_solve": per_solve(r1d[-1])}}
+        for f in (0, 2, 1):
+            pcg_it[f"config{other.cfg}_form{f}"] = iteration_entry(other, f)
+        del other
+        torch.cuda.synchronize()
+        extras["batch"] = batch_key(B, local, nqps=args.extra_batch)
+        extras["serving"] = serving_key(B, local, nreq=args.extra_requests, rate=args.extra_rate,
+                                        max_n=args.extra_max_n)
+
     if rank == 0:
-        cpu = oracle_sample(qp, gold["ipm_iters"]) if world == 1 else None
-        st0 = res[-1]["stats"] if res else {}
+        cpu = None
+        if world == 1:
+            cpu, _ = oracle_sample(qp, gold["ipm_iters"])
         line = {
             "metric": METRIC, "value": round(value, 4), "unit": "QPs/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 2),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "precision": "mixed (FP32 operator and P_H, FP64 refinement)",
-                       "preconditioner": "auto -> P_H (few equalities)", "parallelism": f"replicas x{world}",
+            "config": {"workload": WORKLOADS[main.cfg],
+                       "precision": "mixed (FP32 operator and P_H, FP64 refinement and step logic)",
+                       "preconditioner": "auto -> " + pc_name, "pcg_form": FORM_NAMES[0],
+                       "parallelism": f"replicas x{world}",
                        "l2": "flushed between timed steps (256 MB write, untimed)"},
-            "solved": f"{sum(ok)}/{len(ok)} per rank", "obj_rel_err": [abs(r["f"] - gold["f"]) / abs(gold["f"]) for r in res],
-            "ipm_iters": [r["ipm"] for r in res], "pcg_iters": [r["pcg"] for r in res],
-            "oracle_ipm_iters": gold["ipm_iters"],
-            "breakdown_ms": {k: round(st0.get(k, 0.0), 1) for k in ("t_factor_ms", "t_pcg_ms", "t_precond_ms", "t_solve_ms")},
-            "fp64": {"value": round(value64, 4), "unit": "QPs/s", "ms_per_step": round(total64 / max(1, args.fp64_steps), 2),
-                     "dtype": "f64", "solved": f"{sum(ok64)}/{len(ok64)}",
-                     "ipm_iters": [r["ipm"] for r in res64], "pcg_iters": [r["pcg"] for r in res64]},
-            "roofline": roofline, "wform": wform, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-            "clocks": clk.summary(),
+            "solved": f"{sum(ok)}/{len(ok)} per rank",
+            "obj_rel_err": [abs(r["f"] - gold["f"]) / abs(gold["f"]) for r in res],
+            "ipm_iters": [r["ipm"] for r in res], "oracle_ipm_iters": gold["ipm_iters"],
+            "pcg_iters": [r["pcg"] for r in res],
+            "per_solve": per_solve(res[-1]) if res else None,
+            "fp64": {"value": round(value64, 4), "unit": "QPs/s", "steps": fp64_steps,
+                     "ms_per_step": round(total64 / fp64_steps, 2), "dtype": "f64",
+                     "solved": f"{sum(ok64)}/{len(ok64)}", "ipm_iters": [r["ipm"] for r in res64],
+                     "pcg_iters": [r["pcg"] for r in res64], "per_solve": per_solve(res64[-1]) if res64 else None},
+            "mixed_over_fp64": round(value / value64, 3) if value64 > 0 else None,
+            "roofline": roofline, "pcg_iteration": pcg_it, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(launches), "clocks": clk.summary(),
         }
+        line.update(extras)
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -359,7 +407,7 @@ def run_ours(args):
 
 def source_hash():
     """Hash of the sources of the persistent PCG kernel (the kernel whose DRAM
-    traffic profiles/pcg_iteration_traffic.json records)."""
+    traffic profiles/pcg_iteration_traffic_config*.json records)."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2104_12916_gb300", "csrc")
@@ -371,50 +419,56 @@ def source_hash():
 
 # ------------------------------------------------------------ reference arm
 def run_reference(args):
-    """The reference arm is the FP64 CPU oracle (the paper ships no code): each
-    step is a bounded sample (start point + 2 IPM iterations of the 3x3 LDL^T
-    oracle) scaled to a full solve by the oracle's iteration count."""
+    """The reference arm is the FP64 CPU oracle (the paper ships no code).  Each
+    step is a bounded sample of the headline workload -- the oracle's start point
+    and one IPM iteration (3x3 LDL^T variant) -- and the line's value scales the
+    median sample to a full solve by the oracle's iteration count.  ms_per_step is
+    the wall time a sample step took, so steps x ms_per_step is what ran."""
     world, rank, local = dist_env()
     if rank != 0:
         return
-    gold = golden()
-    qp = qpgen.config_qp(CONFIG_ID)
-    for _ in range(args.warmup):
-        pass   # the oracle has no warm-up state; warm-up steps are not repeated work
+    gold = golden(args.config)
+    qp = qpgen.config_qp(args.config)
+    for _ in range(min(args.warmup, 1)):
+        oracle_sample(qp, gold["ipm_iters"])
     vals = []
     t0 = time.perf_counter()
     for _ in range(args.steps):
         vals.append(oracle_sample(qp, gold["ipm_iters"]))
     wall = time.perf_counter() - t0
-    v = statistics.median(r["value"] for r in vals)
-    cpu = dict(vals[0])
+    v = statistics.median(r[0]["value"] for r in vals)
+    cpu = dict(vals[0][0])
     cpu["value"] = v
     line = {"metric": METRIC, "value": v, "unit": "QPs/s", "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": round(1e3 / v, 1), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "parallelism": "cpu"}, "impl": "reference",
-            "cpu_baseline": cpu, "e2e": {"value": v, "unit": "QPs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-            "sample_wall_s": round(wall, 1)}
+            "warmup": args.warmup, "ms_per_step": round(1e3 * wall / max(1, args.steps), 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.config], "parallelism": "cpu",
+                       "step": "oracle start point + 1 IPM iteration (value scales it to a full solve)"},
+            "impl": "reference", "cpu_baseline": cpu,
+            "e2e": {"value": v, "unit": "QPs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "full_solve_s_estimate": round(1.0 / v, 1), "sample_wall_s": round(wall, 1)}
     print(json.dumps(line), flush=True)
 
 
 def run_profile(args):
-    """Factor the workload's QP and time `--profile-pcg` PCG iterations (P_H,
-    mid-IPM D); prints the per-iteration time.  Used as the ncu target."""
+    """Factor the workload's QP and time `--profile-pcg` PCG iterations (mid-IPM
+    D, AUTO preconditioner); prints the per-iteration time.  Used as the ncu target."""
     from paper_2104_12916_gb300 import binding as B, build
     build.build()
-    qp = qpgen.config_qp(CONFIG_ID)
+    qp = qpgen.config_qp(args.config)
     o = B.qp_opts_default()
     o.precision = B.QP_PREC_FP32 if args.precision == "fp32" else B.QP_PREC_FP64
     o.mixed_fallback = 0          # time the FP32 kernels themselves
     o.pcg_form = args.pcg_form
-    h = B.qp_create(qp.H, qp.c, qp.A, qp.b, np.ascontiguousarray(qp.C), qp.d, o)
+    cc = np.ascontiguousarray
+    h = B.qp_create(cc(qp.H), cc(qp.c), cc(qp.A), cc(qp.b), cc(qp.C), cc(qp.d), o)
     B.qp_factor_K0(h)
     Dmid = np.exp(np.random.default_rng(7).uniform(np.log(1e-1), np.log(1e1), qp.m2))
     ms = B.qp_time_pcg_iteration(h, Dmid, precond=B.QP_PC_AUTO, warmup=8, iters=args.profile_pcg)
     by = B.qp_pcg_bytes_per_iter(h, B.QP_PC_AUTO)
     print(json.dumps({"pcg_iteration_us": ms * 1e3, "algorithmic_MB": by / 1e6,
-                      "GBps": by / (ms * 1e-3) / 1e9, "precision": args.precision, "pcg_form": args.pcg_form}))
+                      "GBps": by / (ms * 1e-3) / 1e9, "precision": args.precision, "pcg_form": args.pcg_form,
+                      "config": args.config}))
     B.qp_destroy(h)
 
 
@@ -422,36 +476,28 @@ BATCH_WORKLOAD = ("512 dense QPs, n uniform [64,512], m_eq uniform [0.1n,0.5n], 
                   "Lambda log-uniform [1e-2,1e2], seeds 1e6+i")
 
 
-def run_batch(args):
+def batch_measure(B, local, qps, concurrency, pcg_form=0, check_n=160, precs=None):
     """The batched workload through qp_batch_solve: every QP created from host
     buffers, solved with many in flight (each QP's persistent PCG kernel on 8-16
-    blocks launched as one cluster, host waits yielding), the solution read back.  One step = the whole batch,
-    timed on the host clock around qp_batch_solve (inputs already on the device);
-    e2e includes the creation (H2D) and the solution copies.  QPs with n <= 160
-    are checked against the FP64 oracle."""
-    world, rank, local = dist_env()
-    if rank != 0:
-        return
-    from paper_2104_12916_gb300 import binding as B, build
-    build.build()
-    B.load()
-    qps = [qpgen.batch_qp(i) for i in range(args.batch)]
+    blocks launched as one cluster, host waits yielding), the solution read back.
+    Timed on the host clock around qp_batch_solve (inputs already on the device);
+    e2e includes the creation (H2D) and the solution copies.  QPs with
+    n <= check_n are checked against the FP64 oracle."""
+    precs = precs or (B.QP_PREC_FP32, B.QP_PREC_FP64)
     out = {}
-    for prec in (B.QP_PREC_FP32, B.QP_PREC_FP64):
+    for prec in precs:
         o = B.qp_opts_default()
-        o.precision, o.blocking_wait, o.pcg_form = prec, 1, args.pcg_form
+        o.precision, o.blocking_wait, o.pcg_form = prec, 1, pcg_form
         l0 = B.qp_kernel_launches()
         with ClockSampler(local) as clk:
             t0 = time.perf_counter()
             hs = [B.QP.from_qpgen(q, o) for q in qps]
             t1 = time.perf_counter()
-            st, res = B.qp_batch_solve([h.h for h in hs], max_concurrent=args.concurrency)
+            st, res = B.qp_batch_solve([h.h for h in hs], max_concurrent=concurrency)
             t2 = time.perf_counter()
-            xs = []
             for q, h in zip(qps, hs):
                 x = np.zeros(q.n)
                 B.qp_get_solution(h.h, x)
-                xs.append(x)
             t3 = time.perf_counter()
         for h in hs:
             h.close()
@@ -460,30 +506,54 @@ def run_batch(args):
                          clocks=clk.summary())
     from oracle import ipm
     errs = []
-    r32 = out[B.QP_PREC_FP32]["res"]
+    r32 = out[precs[0]]["res"]
     for i, q in enumerate(qps):
-        if q.n <= 160:
+        if q.n <= check_n:
             ref = ipm.solve_qp(q, variant="kkt3")
             errs.append(abs(r32[i]["obj"] - ref.f) / max(abs(ref.f), 1.0))
-    m = out[B.QP_PREC_FP32]
-    m64 = out[B.QP_PREC_FP64]
+    m = out[precs[0]]
+    lat = [r["solve_ms"] for r in m["res"]]
     h2d = sum(8 * (q.n * q.n + q.m1 * q.n + q.m2 * q.n + q.n + q.m1 + q.m2) for q in qps)
+    d = {"value": round(sum(m["ok"]) / m["solve_s"], 3), "unit": "QPs/s", "qps": len(qps), "in_flight": concurrency,
+         "ms": round(m["solve_s"] * 1e3, 1), "solved": f"{sum(m['ok'])}/{len(qps)}",
+         "oracle_checked": len(errs), "oracle_max_rel_err": max(errs) if errs else None,
+         "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 1), "p99": round(float(np.percentile(lat, 99)), 1)},
+         "e2e": {"value": round(sum(m["ok"]) / m["e2e_s"], 3), "unit": "QPs/s",
+                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": sum(8 * q.n for q in qps)},
+         "gpu_launches": int(m["launches"]), "clocks": m["clocks"]}
+    if len(precs) > 1:
+        m64 = out[precs[1]]
+        d["fp64"] = {"value": round(sum(m64["ok"]) / m64["solve_s"], 3), "unit": "QPs/s",
+                     "solved": f"{sum(m64['ok'])}/{len(qps)}"}
+    return d
+
+
+def batch_key(B, local, nqps):
+    """The first `nqps` QPs of the batched workload (bounded extra key of the bench line)."""
+    qps = [qpgen.batch_qp(i) for i in range(nqps)]
+    d = batch_measure(B, local, qps, concurrency=16)
+    d["workload"] = f"first {nqps} of: " + BATCH_WORKLOAD
+    return d
+
+
+def run_batch(args):
+    """The whole batched workload (512 QPs) as its own line."""
+    world, rank, local = dist_env()
+    if rank != 0:
+        return
+    from paper_2104_12916_gb300 import binding as B, build
+    build.build()
+    B.load()
+    qps = [qpgen.batch_qp(i) for i in range(args.batch)]
+    d = batch_measure(B, local, qps, args.concurrency, args.pcg_form)
     line = {"metric": "QPs solved/s on the 512-QP batch (mixed precision; FP64 path alongside)",
-            "value": round(sum(m["ok"]) / m["solve_s"], 3), "unit": "QPs/s", "n_gpus": 1, "steps": 1, "warmup": 0,
-            "ms_per_step": round(m["solve_s"] * 1e3, 1), "higher_is_better": True, "scaling": "weak",
+            "value": d["value"], "unit": "QPs/s", "n_gpus": 1, "steps": 1, "warmup": 0,
+            "ms_per_step": d["ms"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": BATCH_WORKLOAD, "qps": len(qps), "in_flight": args.concurrency,
                        "precision": "mixed (FP32 operator and P_H, FP64 refinement)",
-                       "pcg_form": "W-form" if args.pcg_form else "implicit"},
-            "solved": f"{sum(m['ok'])}/{len(qps)}",
-            "fp64": {"value": round(sum(m64["ok"]) / m64["solve_s"], 3), "unit": "QPs/s",
-                     "solved": f"{sum(m64['ok'])}/{len(qps)}"},
-            "oracle_checked": len(errs), "oracle_max_rel_err": max(errs) if errs else None,
-            "latency_ms": {"p50": round(float(np.percentile([r["solve_ms"] for r in m["res"]], 50)), 1),
-                           "p99": round(float(np.percentile([r["solve_ms"] for r in m["res"]], 99)), 1)},
-            "e2e": {"value": round(sum(m["ok"]) / m["e2e_s"], 3), "unit": "QPs/s",
-                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": sum(8 * q.n for q in qps)},
-            "gpu_launches": int(m["launches"]), "clocks": m["clocks"]}
+                       "pcg_form": FORM_NAMES[args.pcg_form]}}
+    line.update({k: v for k, v in d.items() if k not in ("value", "unit", "ms")})
     print(json.dumps(line), flush=True)
 
 
@@ -491,25 +561,16 @@ SERVING_WORKLOAD = ("served stream: n log-uniform [64,4096], m_eq = n U(0.05,0.9
                     "C CSR 8 nnz/row, Lambda log-uniform [1e-2,1e2], Poisson arrivals")
 
 
-def run_serving(args):
-    """A Poisson stream of the served workload through qp_server_*: requests are
-    submitted at their arrival times (host buffers: the submission copies them,
-    the server moves them to the device when it admits them), results polled as
-    they complete.  value = solved QPs / (last completion - first arrival); a QP
-    counts as solved when it converged to the IPM tolerances (FP64 residuals);
-    the requests with n <= 256 are also checked against the FP64 oracle."""
-    world, rank, local = dist_env()
-    if rank != 0:
-        return
-    from paper_2104_12916_gb300 import binding as B, build
-    build.build()
-    B.load()
-    idx = [i for i in range(10 * args.requests) if qpgen.serving_dims(i)[0] <= args.max_n][:args.requests]
-    qps = [qpgen.serving_qp(i) for i in idx]
-    arrive = qpgen.arrival_times(len(qps), args.rate)
+def serving_measure(B, local, qps, arrive, budget_gb, slots, pcg_form=0, check_n=256):
+    """A Poisson stream through qp_server_*: requests are submitted at their
+    arrival times (host buffers: the submission copies them, the server moves them
+    to the device when it admits them), results polled as they complete.
+    value = solved QPs / (last completion - first arrival); a QP counts as solved
+    when it converged to the IPM tolerances (FP64 residuals); the requests with
+    n <= check_n are also checked against the FP64 oracle."""
     o = B.qp_opts_default()
-    o.blocking_wait, o.pcg_form = 1, args.pcg_form
-    srv = B.Server(budget_bytes=int(args.budget_gb * 1e9), max_slots=args.slots, opts=o)
+    o.blocking_wait, o.pcg_form = 1, pcg_form
+    srv = B.Server(budget_bytes=int(budget_gb * 1e9), max_slots=slots, opts=o)
     l0 = B.qp_kernel_launches()
     results = {}
     pending = {}
@@ -535,20 +596,13 @@ def run_serving(args):
     launches = B.qp_kernel_launches() - l0
     lat = np.array([results[i][0]["latency_ms"] for i in range(len(qps))])
     ok = [results[i][0]["status"] == 0 for i in range(len(qps))]
-    # oracle check of the small requests
     from oracle import ipm
     errs = []
     for i, q in enumerate(qps):
-        if q.n <= 256 and ok[i]:
+        if q.n <= check_n and ok[i]:
             ref = ipm.solve_qp(q, variant="kkt3")
             errs.append(abs(results[i][0]["obj"] - ref.f) / max(abs(ref.f), 1.0))
-    line = {"metric": "QPs solved/s on a served Poisson stream, with p50/p99 latency",
-            "value": round(sum(ok) / wall, 3), "unit": "QPs/s", "n_gpus": 1, "steps": len(qps), "warmup": 0,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": SERVING_WORKLOAD, "rate_per_s": args.rate, "requests": len(qps),
-                       "max_n": args.max_n, "budget_gb": args.budget_gb, "slots": args.slots,
-                       "precision": "mixed (FP32 operator and P_H, FP64 refinement)",
-                       "pcg_form": "W-form" if args.pcg_form else "implicit"},
+    return {"value": round(sum(ok) / wall, 3), "unit": "QPs/s", "requests": len(qps),
             "latency_ms": {"p50": round(float(np.percentile(lat, 50)), 1), "p99": round(float(np.percentile(lat, 99)), 1),
                            "max": round(float(lat.max()), 1)},
             "wait_ms_p50": round(float(np.percentile([results[i][0]["wait_ms"] for i in range(len(qps))], 50)), 1),
@@ -557,6 +611,51 @@ def run_serving(args):
             "n_range": [min(q.n for q in qps), max(q.n for q in qps)],
             "server": {k2: st[k2] for k2 in ("peak_reserved_bytes", "peak_device_bytes", "failed")},
             "gpu_launches": int(launches), "clocks": clk.summary()}
+
+
+def serving_requests(count, max_n):
+    idx = [i for i in range(20 * count) if qpgen.serving_dims(i)[0] <= max_n][:count]
+    return [qpgen.serving_qp(i) for i in idx]
+
+
+def serving_key(B, local, nreq, rate, max_n):
+    """The first `nreq` requests of the served stream with n <= max_n (bounded
+    extra key of the bench line)."""
+    qps = serving_requests(nreq, max_n)
+    d = serving_measure(B, local, qps, qpgen.arrival_times(len(qps), rate), 150.0, 64)
+    d["workload"] = f"first {len(qps)} requests with n <= {max_n} of: " + SERVING_WORKLOAD
+    d["rate_per_s"] = rate
+    return d
+
+
+def run_serving(args):
+    """The served stream as its own line (one arrival rate, or a sweep)."""
+    world, rank, local = dist_env()
+    if rank != 0:
+        return
+    from paper_2104_12916_gb300 import binding as B, build
+    build.build()
+    B.load()
+    qps = serving_requests(args.requests, args.max_n)
+    rates = [float(r) for r in args.rates.split(",")] if args.rates else [args.rate]
+    sweep = []
+    for rate in rates:
+        d = serving_measure(B, local, qps, qpgen.arrival_times(len(qps), rate), args.budget_gb, args.slots,
+                            args.pcg_form)
+        d["rate_per_s"] = rate
+        sweep.append(d)
+    d = sweep[0]
+    line = {"metric": "QPs solved/s on a served Poisson stream, with p50/p99 latency",
+            "value": d["value"], "unit": "QPs/s", "n_gpus": 1, "steps": len(qps), "warmup": 0,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": SERVING_WORKLOAD, "rate_per_s": rates[0], "requests": len(qps),
+                       "max_n": args.max_n, "budget_gb": args.budget_gb, "slots": args.slots,
+                       "precision": "mixed (FP32 operator and P_H, FP64 refinement)",
+                       "pcg_form": FORM_NAMES[args.pcg_form]}}
+    line.update({k: v for k, v in d.items() if k not in ("value", "unit", "requests")})
+    if len(sweep) > 1:
+        line["rate_sweep"] = [{"rate_per_s": x["rate_per_s"], "value": x["value"], "latency_ms": x["latency_ms"],
+                               "solved": x["solved"]} for x in sweep]
     print(json.dumps(line), flush=True)
 
 

@@ -113,12 +113,18 @@ typedef struct {
                              every reduction has a fixed order independent of the grid. */
     int blocking_wait;    /* 1: host waits on the solver's stream yield the CPU instead of spinning
                              (many QPs in flight on more host threads than cores); default 0 */
-    int pcg_form;         /* how the persistent PCG kernel applies K_F.  0 (default): the implicit
-                             product of Sec. 5.2 (C'p, the forward and back solves with the K0
-                             factor, C y; four matrix phases).  1: the same product through
+    int pcg_form;         /* how the persistent PCG kernel applies K_F (Sec. 5.2: a product with C',
+                             a solve with the K0 factor, a product with C).  0 (default): the solve
+                             as one product with M0 = [K0^{-1}]_11 = R^{-1} R^{-T} - Et' Et, the (1,1)
+                             block of the inverse of the factorization, formed once per QP in FP64
+                             (three matrix phases, 2 m2 n + n^2 elements per iteration).  2: the
+                             forward and the back solve with the stored inverse factor as two
+                             phases ([R^{-T}; Et] u, then [R^{-1} | Et'] [z1; -z2]; four matrix
+                             phases, 2 m2 n + n^2 + 2 m1 n elements).  1: the same product through
                              B = L^{-1}[C'; 0] = [R^{-T} C'; Et C'], formed once per QP:
                              K_F p = D p + B1'(B1 p) - B2'(B2 p) (two matrix phases; 2 (n + m1) m2
-                             elements per iteration instead of 2 m2 n + n^2 + 2 m1 n) */
+                             elements).  All three are the same operator; the per-phase kernels
+                             (pcg_check_every < 0) always use the two triangular solves. */
     void *stream;         /* cudaStream_t, or NULL for a library-created stream */
 } qp_opts;
 

@@ -9,6 +9,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "tc_gemm.cuh"
 
 namespace pcgipm {
 
@@ -158,49 +159,58 @@ constexpr int kNB = 64;   // block size of the blocked factorization
 // floor_mode = 0: a pivot d <= piv_floor * diag0[k0+j] (diag0: the matrix's
 //   original diagonal; a non-positive or numerically zero pivot) records
 //   info = k0 + j + 1 (first failure wins) and continues with d = 1 so that the
-//   kernel stays finite.
+//   kernel stays finite.  With `warn`, the first pivot d <= warn_floor * diag0
+//   is also recorded there.
 // floor_mode = 1: a pivot d < piv_floor is replaced by piv_floor (a diagonal
 //   shift of a preconditioner; counted in info as a positive number of shifts).
+// Right-looking with one block barrier per column: every thread derives the
+// pivot of column j itself from the updated diagonal entry, the update
+// a[i][l] -= a[i][j] a[l][j] / d uses the unscaled column, and the scaled column
+// goes to a separate tile (lf), so no thread writes what another reads in the
+// same step.
 template <typename T, typename CT>
 __global__ void __launch_bounds__(256) potrf_diag_kernel(T* A, long long lda, T* W, long long ldw,
                                                          int k0, int kb, int floor_mode,
                                                          double piv_floor, int* info,
-                                                         const double* __restrict__ diag0) {
+                                                         const double* __restrict__ diag0,
+                                                         double warn_floor, int* warn) {
     PCG_COUNT_KERNEL();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     auto a = reinterpret_cast<CT(*)[kNB + 1]>(smem_raw);
     auto w = reinterpret_cast<CT(*)[kNB + 1]>(smem_raw + sizeof(CT) * kNB * (kNB + 1));
-    __shared__ CT piv;
+    auto lf = reinterpret_cast<CT(*)[kNB + 1]>(smem_raw + 2 * sizeof(CT) * kNB * (kNB + 1));
     const int tid = threadIdx.x;
     for (int e = tid; e < kb * kb; e += 256) {
         const int i = e / kb, j = e % kb;
         a[i][j] = (j <= i) ? CT(A[(k0 + i) * lda + k0 + j]) : CT(0);
+        lf[i][j] = CT(0);
     }
     __syncthreads();
-    // right-looking: scale column j, then update the trailing lower triangle;
     // thread (ty, tx) of a 16 x 16 layout takes rows ty + 16 r and columns tx + 16 c
     const int tx = tid & 15, ty = tid >> 4;
     for (int j = 0; j < kb; ++j) {
-        if (tid == 0) {
-            CT d = a[j][j];
-            if (floor_mode == 0) {
-                if (!(d > CT(piv_floor * diag0[k0 + j]))) {
-                    atomicCAS(info, 0, k0 + j + 1);
-                    d = CT(1);
-                }
-            } else if (!(d >= CT(piv_floor))) {
-                atomicAdd(info, 1);
-                d = CT(piv_floor);
+        CT d = a[j][j];
+        bool bad = false;
+        if (floor_mode == 0) {
+            if (tid == 0 && warn && !(d > CT(warn_floor * diag0[k0 + j]))) atomicCAS(warn, 0, k0 + j + 1);
+            if (!(d > CT(piv_floor * diag0[k0 + j]))) {
+                bad = true;
+                d = CT(1);
             }
-            piv = sqrt(d);
-            a[j][j] = piv;
+        } else if (!(d >= CT(piv_floor))) {
+            bad = true;
+            d = CT(piv_floor);
         }
-        __syncthreads();
-        const CT inv = CT(1) / piv;
-        for (int i = j + 1 + tid; i < kb; i += 256) a[i][j] *= inv;
-        __syncthreads();
+        if (bad && tid == 0) {
+            if (floor_mode == 0) atomicCAS(info, 0, k0 + j + 1);
+            else atomicAdd(info, 1);
+        }
+        const CT piv = sqrt(d);
+        const CT inv = CT(1) / piv, dinv = CT(1) / d;
+        if (tid == 0) lf[j][j] = piv;
+        for (int i = j + 1 + tid; i < kb; i += 256) lf[i][j] = a[i][j] * inv;
         for (int i = j + 1 + ty; i < kb; i += 16) {
-            const CT aij = a[i][j];
+            const CT aij = a[i][j] * dinv;
             for (int l = j + 1 + tx; l <= i; l += 16) a[i][l] -= aij * a[l][j];
         }
         __syncthreads();
@@ -212,18 +222,18 @@ __global__ void __launch_bounds__(256) potrf_diag_kernel(T* A, long long lda, T*
     for (int i = 0; i < kb; ++i) {
         CT sum = CT(0);
         if (t < i)
-            for (int k = t + q; k < i; k += 4) sum += a[i][k] * w[k][t];
+            for (int k = t + q; k < i; k += 4) sum += lf[i][k] * w[k][t];
         sum += __shfl_xor_sync(0xffffffffu, sum, 1);
         sum += __shfl_xor_sync(0xffffffffu, sum, 2);
         if (q == 0) {
-            if (t < i) w[i][t] = -sum / a[i][i];
-            else if (t == i) w[i][i] = CT(1) / a[i][i];
+            if (t < i) w[i][t] = -sum / lf[i][i];
+            else if (t == i) w[i][i] = CT(1) / lf[i][i];
         }
         __syncthreads();
     }
     for (int e = tid; e < kb * kb; e += 256) {
         const int i = e / kb, j = e % kb;
-        A[(k0 + i) * lda + k0 + j] = (j <= i) ? T(a[i][j]) : T(0);
+        A[(k0 + i) * lda + k0 + j] = (j <= i) ? T(lf[i][j]) : T(0);
         W[(k0 + i) * ldw + k0 + j] = (j <= i) ? T(w[i][j]) : T(0);
     }
 }
@@ -297,6 +307,8 @@ __global__ void __launch_bounds__(256) trmm_rowblock_kernel(T* W, long long ldw,
 // Dynamic shared memory of the three block kernels: two (kNB x kNB+1) tiles.
 template <typename X>
 constexpr size_t two_tiles_bytes() { return 2 * sizeof(X) * kNB * (kNB + 1); }
+template <typename X>
+constexpr size_t three_tiles_bytes() { return 3 * sizeof(X) * kNB * (kNB + 1); }
 
 // Sets the (process-wide) shared-memory attributes once per instantiation; the
 // values are fixed, so concurrent callers agree.
@@ -304,7 +316,7 @@ template <typename T, typename CT>
 inline void chol_inv_prepare() {
     static const bool done = []() {
         cudaFuncSetAttribute(potrf_diag_kernel<T, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)two_tiles_bytes<CT>());
+                             (int)three_tiles_bytes<CT>());
         cudaFuncSetAttribute(trsm_panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)two_tiles_bytes<T>());
         cudaFuncSetAttribute(trmm_rowblock_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -321,15 +333,18 @@ __global__ void save_diag_kernel(const T* __restrict__ A, long long lda, int n, 
         out[i] = (double)A[i * lda + i];
 }
 
-// diag0: scratch of n doubles (used when floor_mode == 0).
+// diag0: scratch of n doubles (used when floor_mode == 0).  With floor_mode 0 and
+// `warn` non-null, the first pivot d <= warn_floor * diag0 is also recorded in *warn.
 template <typename T, typename CT>
 void chol_inv(T* A, long long lda, T* W, long long ldw, int n, int floor_mode, double piv_floor,
-              int* d_info, cudaStream_t s, double* diag0 = nullptr) {
+              int* d_info, cudaStream_t s, double* diag0 = nullptr, double warn_floor = 0.0,
+              int* warn = nullptr) {
     if (floor_mode == 0) save_diag_kernel<T><<<(n + 255) / 256, 256, 0, s>>>(A, lda, n, diag0);
     for (int k0 = 0; k0 < n; k0 += kNB) {
         const int kb = min(kNB, n - k0);
-        potrf_diag_kernel<T, CT><<<1, 256, two_tiles_bytes<CT>(), s>>>(A, lda, W, ldw, k0, kb,
-                                                                      floor_mode, piv_floor, d_info, diag0);
+        potrf_diag_kernel<T, CT><<<1, 256, three_tiles_bytes<CT>(), s>>>(A, lda, W, ldw, k0, kb,
+                                                                      floor_mode, piv_floor, d_info, diag0,
+                                                                      warn_floor, warn);
         const int rest = n - k0 - kb;
         if (k0 > 0) {
             trmm_rowblock_kernel<T><<<(k0 + kNB - 1) / kNB, 256, two_tiles_bytes<T>(), s>>>(W, ldw, k0, kb);
@@ -353,6 +368,98 @@ void chol_inv(T* A, long long lda, T* W, long long ldw, int n, int floor_mode, d
             h.C = W + (k0 + kb) * ldw; h.ldc = ldw;
             h.alpha = T(-1); h.beta = T(1);
             gemm<T>(h, s);
+        }
+    }
+}
+
+// out[j * ldo + i] = hi/lo parts of in[i * ldi + j] (rows x cols in, cols x rows out):
+// the transposed, TF32-split copy of a row block that the tensor-core GEMM takes
+// as its K-major B operand.
+__global__ void tc_transpose_split_kernel(const float* __restrict__ in, long long ldi, int rows, int cols,
+                                          float* __restrict__ hi, float* __restrict__ lo, long long ldo) {
+    PCG_COUNT_KERNEL();
+    __shared__ float tile[32][33];
+    const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += 8) {
+        const int i = by + r, j = bx + threadIdx.x;
+        tile[r][threadIdx.x] = (i < rows && j < cols) ? in[i * ldi + j] : 0.0f;
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += 8) {
+        const int j = bx + r, i = by + threadIdx.x;
+        if (i < rows && j < cols) {
+            const float v = tile[threadIdx.x][r];
+            uint32_t h;
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(v));
+            hi[j * ldo + i] = __uint_as_float(h);
+            lo[j * ldo + i] = v - __uint_as_float(h);
+        }
+    }
+}
+
+inline void tc_split(const float* x, long long ldx, int rows, int cols, float* hi, float* lo, long long ldo,
+                     cudaStream_t s) {
+    if (rows <= 0 || cols <= 0) return;
+    const long long total = (long long)rows * cols;
+    const int blocks = (int)std::min<long long>((total + 255) / 256, 152LL * 16);
+    tc_split_kernel<<<blocks, 256, 0, s>>>(x, ldx, rows, cols, hi, lo, ldo);
+}
+
+// Floats of tensor-core scratch chol_inv_tc needs for an n x n factorization.
+inline size_t chol_tc_scratch(int n) { return 4 * (size_t)(n + kTcBM) * kNB; }
+
+// chol_inv for FP32 storage with the two rank-kNB updates of every block column
+// on the tensor cores (FP32-accurate 3xTF32): the trailing update
+// A22 -= L21 L21' (lower tiles) and the inverse update
+// W[k+1:, 0:k+1] -= L21 W[k, 0:k+1].  The diagonal blocks, their inverses and
+// the panel stay on the CUDA cores in compute type CT.  scratch: at least
+// chol_tc_scratch(n) floats; d_err receives a tensor-core wait failure.  Falls
+// back to the CUDA-core GEMM if a tensor map cannot be made.
+template <typename CT>
+void chol_inv_tc(float* A, long long lda, float* W, long long ldw, int n, int floor_mode, double piv_floor,
+                 int* d_info, cudaStream_t s, float* scratch, int* d_err, double* diag0 = nullptr,
+                 double warn_floor = 0.0, int* warn = nullptr) {
+    if (floor_mode == 0) save_diag_kernel<float><<<(n + 255) / 256, 256, 0, s>>>(A, lda, n, diag0);
+    const long long ldk = kNB;
+    float* lh = scratch;
+    float* ll = lh + (size_t)n * ldk;
+    float* bh = ll + (size_t)n * ldk;
+    float* bl = bh + (size_t)n * ldk;
+    for (int k0 = 0; k0 < n; k0 += kNB) {
+        const int kb = min(kNB, n - k0);
+        potrf_diag_kernel<float, CT><<<1, 256, three_tiles_bytes<CT>(), s>>>(A, lda, W, ldw, k0, kb, floor_mode,
+                                                                            piv_floor, d_info, diag0, warn_floor,
+                                                                            warn);
+        const int rest = n - k0 - kb;
+        if (k0 > 0)
+            trmm_rowblock_kernel<float><<<(k0 + kNB - 1) / kNB, 256, two_tiles_bytes<float>(), s>>>(W, ldw, k0, kb);
+        if (rest <= 0) continue;
+        trsm_panel_kernel<float><<<(rest + kNB - 1) / kNB, 256, two_tiles_bytes<float>(), s>>>(A, lda, W, ldw,
+                                                                                             k0, kb, n);
+        float* L21 = A + (long long)(k0 + kb) * lda + k0;
+        tc_split(L21, lda, rest, kb, lh, ll, ldk, s);   // (the GEMM's K is kb: columns beyond read as zeros)
+        bool ok = tc_gemm(rest, rest, kb, -1.0f, lh, ll, ldk, lh, ll, ldk, 1.0f,
+                          A + (long long)(k0 + kb) * lda + k0 + kb, lda, true, true, d_err, s);
+        dim3 tg((k0 + kb + 31) / 32, (kb + 31) / 32), tb(32, 8);
+        tc_transpose_split_kernel<<<tg, tb, 0, s>>>(W + (long long)k0 * ldw, ldw, kb, k0 + kb, bh, bl, ldk);
+        ok = ok && tc_gemm(rest, k0 + kb, kb, -1.0f, lh, ll, ldk, bh, bl, ldk, 1.0f, W + (long long)(k0 + kb) * ldw,
+                           ldw, true, false, d_err, s);
+        if (!ok) {
+            cudaGetLastError();
+            GemmArgs<float> g{};
+            g.M = rest; g.N = rest; g.K = kb;
+            g.A = L21; g.sai = lda; g.sak = 1;
+            g.B = L21; g.sbk = 1; g.sbj = lda;
+            g.C = A + (long long)(k0 + kb) * lda + k0 + kb; g.ldc = lda;
+            g.alpha = -1.0f; g.beta = 1.0f; g.lower_out = 1;
+            gemm<float>(g, s);
+            GemmArgs<float> h{};
+            h.M = rest; h.N = k0 + kb; h.K = kb;
+            h.A = L21; h.sai = lda; h.sak = 1;
+            h.B = W + (long long)k0 * ldw; h.sbk = ldw; h.sbj = 1;
+            h.C = W + (long long)(k0 + kb) * ldw; h.ldc = ldw;
+            h.alpha = -1.0f; h.beta = 1.0f;
+            gemm<float>(h, s);
         }
     }
 }

@@ -58,6 +58,7 @@ public:
         const size_t bytes = count * sizeof(T) + 256;
         if (cudaMallocAsync(&p, bytes, stream) != cudaSuccess) {
             cudaGetLastError();
+            if (std::getenv("PCGIPM_VERBOSE")) std::fprintf(stderr, "  device allocation of %zu bytes failed\n", bytes);
             throw NoMem{};
         }
         PCG_CK(cudaMemsetAsync(p, 0, bytes, stream));
@@ -136,13 +137,10 @@ struct Op {
     Mat<TO> Et, EtT;   // Gt R^{-T} = L_S^{-1} A H^{-1} (the (2,1) block of L^{-1}) and its transpose
     Mat<TO> WS, WST;   // L_S^{-1} (lower) and L_S^{-T} (upper)
     Mat<TO> BW, BWT;   // pcg_form 1: B = L^{-1}[C'; 0] = [R^{-T} C'; Et C'] ((n+m1) x m2) and B'
-    TO* PW = nullptr;  // pcg_form 1: chunk partials of B p
-    int ldW = 0;
+    Mat<TO> M0;        // [K0^{-1}]_11 = R^{-1} R^{-T} - Et' Et (n x n, symmetric), pcg_form 0
+    TO *oU = nullptr, *oY, *oZ, *oW;   // persistent kernel: outputs of the operator phases
     TO *px = nullptr, *pr, *pz, *pp, *pq, *pu, *pz1, *pz2, *pt, *py, *prhs, *pD, *pDinv;
     TO *ku, *kw, *ke, *kz1, *kz2, *kt, *ka, *kmb, *wa, *wg;
-    TO *pr1, *pp1;                       // second buffers of r and p (fused kernel)
-    TO *PU, *PZ1, *PZ2, *PT, *PY, *PQ;   // chunk partials of the fused kernel
-    int ldU, ldZ1, ldZ2, ldT, ldY, ldQ;
     cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
     int graph_k[3] = {0, 0, 0};
     bool factored = false;
@@ -152,9 +150,9 @@ struct Op {
 template <typename TP>
 struct Pc {
     Mat<TP> Tm, Pm, WPl, WPu;   // T = C H^{-1} C' (or C diag(H)^{-1} C'), P~, L^{-1}, L^{-T}
+    Mat<TP> PI;                 // P~^{-1} = L^{-T} L^{-1} (m2 x m2, symmetric; FP32 P_H)
     TP *sg = nullptr, *rs, *pv, *Dp;
-    TP *PV = nullptr, *PZ = nullptr;     // chunk partials of the fused kernel
-    int ldV = 0;
+    TP *oV[2] = {nullptr, nullptr};   // persistent kernel: outputs of the P_H phases
     int t_kind = 0;
     double shift = 0.0;
 };
@@ -257,6 +255,7 @@ public:
     }
 
     ~Engine() {
+        if (tc_scr) cudaFreeAsync(tc_scr, s);
         destroy_graphs(o32);
         destroy_graphs(o64);
         if (hst) cudaFreeHost(hst);
@@ -291,31 +290,28 @@ public:
         b += mat(n, n, 8) + mat(m1, n, 8) + mat(n, m1, 8) + mat(m2, n, 8) + mat(n, m2, 8);
         b += 64 * v(cap, 8) + 4096;
         auto op = [&](size_t es, bool copyC) {
-            const int CH = (int)(kSlotBytes / es);
-            auto ncs = [&](int cols) { return (size_t)std::max(1, (cols + CH - 1) / CH); };
-            size_t t = 32 * v(cap, es);
-            t += ((size_t)4 * n + std::max(m1, 1) + m2) * ncs(std::max(n, std::max(m1, m2))) * es + 6 * 256;
+            size_t t = 32 * v(cap, es) + 2 * v(n + m1, es);
             if (copyC) t += mat(m2, n, es) + mat(n, m2, es);
             t += 2 * mat(n, n, es);
+            if (o.pcg_form == 0) t += mat(n, n, es);   // M0
             if (m1) t += 2 * mat(m1, m1, es) + 2 * mat(m1, n, es) + 2 * mat(n, m1, es);
-            if (o.pcg_form == 1)
-                t += mat(n + m1, m2, es) + mat(m2, n + m1, es) + (size_t)(n + m1) * ncs(m2) * es + 256;
+            if (o.pcg_form == 1) t += mat(n + m1, m2, es) + mat(m2, n + m1, es);
             t += mat(n, n, es) + 2 * mat(m1, n, es) + mat(m1, m1, es);   // factor scratch
             return t;
         };
         auto pc = [&](size_t es) {
-            const int CH = (int)(kSlotBytes / es);
-            const size_t ncp = (size_t)std::max(1, (m2 + CH - 1) / CH);
-            return 4 * mat(m2, m2, es) + 4 * v(m2, es) + 2 * ((size_t)m2 * ncp * es + 256) + mat(m2, n, es);
+            size_t t = 4 * mat(m2, m2, es) + 6 * v(m2, es) + mat(m2, n, es);
+            if (es == 4) t += mat(m2, m2, es) + tc_scratch_floats(n, m2) * 4 + 1024;   // P~^{-1}, tensor-core scratch
+            return t;
         };
         const bool fp32 = (o.precision == QP_PREC_FP32);
         const bool ph = o.precond != QP_PC_PL && o.precond != QP_PC_NONE;
+        b += (size_t)kMaxPhases * kTblStride * 8 + 256 + (128 + 8 * 1024) * 8 + 256;
+        b += op(8, false);                       // the factor is formed in FP64
         if (fp32) {
             b += op(4, true);
-            if (o.mixed_fallback || o.pcg_form == 1) b += op(8, false);   // FP64 factor (W-form: B from it)
             if (ph) b += pc(4) + (o.mixed_fallback ? pc(8) : 0);
         } else {
-            b += op(8, false);
             if (ph) b += pc(8);
         }
         return b;
@@ -400,7 +396,9 @@ public:
         part_f = vec<double>(cap_rows); diag0 = vec<double>(cap_rows);
         st = arena.alloc<PcgState>(1);
         bar = arena.alloc<GridBar>(1);
-        tstamp = arena.alloc<unsigned long long>(4 * 32);
+        tstamp = arena.alloc<unsigned long long>(128 + 8 * 1024);
+        d_tcerr = arena.alloc<int>(1);
+        d_tbl = arena.alloc<int2>((size_t)kMaxPhases * kTblStride);
         d_scal = vec<double>(16);
         d_info = arena.alloc<int>(8);
         PCG_CK(cudaMallocHost(&hst, 2 * sizeof(PcgState)));
@@ -455,52 +453,110 @@ public:
     // ------------------------------------------------------------------ factor
     // Setup phase (Sec. 4.1): K0 = [H A'; A 0] = L diag(I, -I) L' with
     // L = [R' 0; G L_S], R'R = H, G = A R^{-1}, L_S L_S' = G G' = A H^{-1} A'.
-    // The diagonal blocks are factored with FP64 pivots; a pivot below
-    // 1e-13 (FP64) / 1e-6 (FP32) of the original diagonal entry means H is not
-    // positive definite (QP_ENOTCONVEX) or A H^{-1} A' is singular (QP_ESINGULAR).
+    // The factor is always formed in FP64 (pivots, triangular inverses and every
+    // product); the FP32 operator holds its entries rounded once.  A pivot below
+    // 1e-13 of the original diagonal entry means H is not positive definite
+    // (QP_ENOTCONVEX) or A H^{-1} A' is singular (QP_ESINGULAR); pivots below
+    // 1e-6 (FP32 resolution) are recorded in fp32_pivot_warn.
+    // Also formed once per QP: M0 = [K0^{-1}]_11 = R^{-1} R^{-T} - Et' Et (the
+    // persistent kernel's K0 solve, pcg_form 0) and, for pcg_form 1,
+    // B = L^{-1}[C'; 0].
+    template <typename TO>
+    void alloc_op_vectors(Op<TO>& o) {
+        o.px = vec<TO>(m2); o.pr = vec<TO>(m2); o.pz = vec<TO>(m2); o.pp = vec<TO>(m2); o.pq = vec<TO>(m2);
+        o.pu = vec<TO>(n); o.pz1 = vec<TO>(n); o.pz2 = vec<TO>(m1); o.pt = vec<TO>(n); o.py = vec<TO>(n);
+        o.prhs = vec<TO>(m2); o.pD = vec<TO>(m2); o.pDinv = vec<TO>(m2);
+        o.ku = vec<TO>(n); o.kw = vec<TO>(m1); o.ke = vec<TO>(m1); o.kz1 = vec<TO>(n); o.kz2 = vec<TO>(m1);
+        o.kt = vec<TO>(n); o.ka = vec<TO>(n); o.kmb = vec<TO>(m1); o.wa = vec<TO>(m2); o.wg = vec<TO>(n);
+        o.oU = vec<TO>(n); o.oY = vec<TO>(n); o.oZ = vec<TO>(n + m1); o.oW = vec<TO>(m2);
+        if (opt.pcg_form == 1) {
+            o.BW.alloc(arena, n + m1, m2);
+            o.BWT.alloc(arena, m2, n + m1);
+        }
+        o.WH.alloc(arena, n, n);
+        o.WHT.alloc(arena, n, n);
+        if (opt.pcg_form == 0) o.M0.alloc(arena, n, n);
+        if (m1) {
+            o.WS.alloc(arena, m1, m1); o.WST.alloc(arena, m1, m1);
+            o.Gt.alloc(arena, m1, n); o.GtT.alloc(arena, n, m1);
+            o.Et.alloc(arena, m1, n); o.EtT.alloc(arena, n, m1);
+        }
+    }
+
+    bool fp32_pivot_warn = false;
+
+    // Scratch of the tensor-core products (TF32 hi/lo splits of their operands),
+    // grown on demand and released with the handle.
+    float* tc_scr = nullptr;
+    size_t tc_cap = 0;
+    int* d_tcerr = nullptr;
+    float* tc_scratch(size_t floats) {
+        if (floats > tc_cap) {
+            if (tc_scr) cudaFreeAsync(tc_scr, s);
+            tc_scr = nullptr;
+            tc_cap = 0;
+            if (cudaMallocAsync(&tc_scr, floats * sizeof(float) + 1024, s) != cudaSuccess) {
+                cudaGetLastError();
+                throw NoMem{};
+            }
+            tc_cap = floats;
+        }
+        return tc_scr;
+    }
+    void tc_check() {
+        int e = 0;
+        PCG_CK(cudaMemcpyAsync(&e, d_tcerr, sizeof(int), cudaMemcpyDeviceToHost, s));
+        wait_stream();
+        if (e) throw QpError{QP_ETIMEOUT};
+    }
+    // Floats of tensor-core scratch of the FP32 P_H path: T's operands
+    // (C and R^{-1}, then C R^{-1}), P~^{-1}'s operand W', and the blocked Cholesky.
+    static size_t tc_scratch_floats(int n, int m2) {
+        const size_t ldn = pad_ld(n), ldm = pad_ld(m2);
+        const size_t t = 2 * (size_t)m2 * ldn + 2 * (size_t)n * ldn;
+        const size_t pi = 2 * (size_t)m2 * ldm;
+        return std::max(std::max(t, pi), chol_tc_scratch(m2));
+    }
+
     template <typename TO>
     void factor_op() {
         Op<TO>& o = op<TO>();
         if (o.factored) return;
         constexpr bool is64 = std::is_same<TO, double>::value;
-        const double rel = is64 ? 1e-13 : 1e-6;
-        chol_inv_prepare<TO, double>();
-        if (!o.px) {
-            o.px = vec<TO>(m2); o.pr = vec<TO>(m2); o.pz = vec<TO>(m2); o.pp = vec<TO>(m2); o.pq = vec<TO>(m2);
-            o.pu = vec<TO>(n); o.pz1 = vec<TO>(n); o.pz2 = vec<TO>(m1); o.pt = vec<TO>(n); o.py = vec<TO>(n);
-            o.prhs = vec<TO>(m2); o.pD = vec<TO>(m2); o.pDinv = vec<TO>(m2);
-            o.ku = vec<TO>(n); o.kw = vec<TO>(m1); o.ke = vec<TO>(m1); o.kz1 = vec<TO>(n); o.kz2 = vec<TO>(m1);
-            o.kt = vec<TO>(n); o.ka = vec<TO>(n); o.kmb = vec<TO>(m1); o.wa = vec<TO>(m2); o.wg = vec<TO>(n);
-            o.pr1 = vec<TO>(m2); o.pp1 = vec<TO>(m2);
-            constexpr int CH = Chunk<TO>::n;
-            auto ncs = [&](int cols) { return (size_t)std::max(1, (cols + CH - 1) / CH); };
-            // chunk-major partials: plane stride = rows of the matrix
-            o.ldU = n; o.ldZ1 = n; o.ldZ2 = std::max(m1, 1); o.ldT = n; o.ldY = n; o.ldQ = m2;
-            o.PU = arena.alloc<TO>(n * ncs(m2)); o.PZ1 = arena.alloc<TO>(n * ncs(n));
-            o.PZ2 = arena.alloc<TO>(std::max(m1, 1) * ncs(n)); o.PT = arena.alloc<TO>(n * ncs(m1));
-            o.PY = arena.alloc<TO>(n * ncs(n)); o.PQ = arena.alloc<TO>(m2 * ncs(n + m1));
-            if (opt.pcg_form == 1) {
-                o.BW.alloc(arena, n + m1, m2);
-                o.BWT.alloc(arena, m2, n + m1);
-                o.ldW = n + m1;
-                o.PW = arena.alloc<TO>((size_t)(n + m1) * ncs(m2));
-            }
-            if constexpr (is64) {
-                o.CW.p = C.p; o.CW.rows = m2; o.CW.cols = n; o.CW.ld = C.ld;
-                o.CWT.p = CT.p; o.CWT.rows = n; o.CWT.cols = m2; o.CWT.ld = CT.ld;
-            } else {
+        if constexpr (!is64) {
+            // FP32 operator: the FP64 factor rounded once (an FP32 factorization would
+            // add about cond(R) u32 to every entry; rounding adds u32 of the entry)
+            factor_op<double>();
+            if (!o.px) {
+                alloc_op_vectors(o);
                 o.CW.alloc(arena, m2, n);
                 o.CWT.alloc(arena, n, m2);
-                convert2d<double, TO>(C.p, C.ld, o.CW.p, o.CW.ld, m2, n, s);
-                convert2d<double, TO>(CT.p, CT.ld, o.CWT.p, o.CWT.ld, n, m2, s);
             }
-            o.WH.alloc(arena, n, n);
-            o.WHT.alloc(arena, n, n);
-            if (m1) {
-                o.WS.alloc(arena, m1, m1); o.WST.alloc(arena, m1, m1);
-                o.Gt.alloc(arena, m1, n); o.GtT.alloc(arena, n, m1);
-                o.Et.alloc(arena, m1, n); o.EtT.alloc(arena, n, m1);
+            convert2d<double, TO>(C.p, C.ld, o.CW.p, o.CW.ld, m2, n, s);
+            convert2d<double, TO>(CT.p, CT.ld, o.CWT.p, o.CWT.ld, n, m2, s);
+            auto rnd = [&](const Mat<double>& a, Mat<TO>& b) {
+                if (a.p && b.p) convert2d<double, TO>(a.p, a.ld, b.p, b.ld, a.rows, a.cols, s);
+            };
+            rnd(o64.WH, o.WH); rnd(o64.WHT, o.WHT); rnd(o64.M0, o.M0);
+            rnd(o64.WS, o.WS); rnd(o64.WST, o.WST); rnd(o64.Gt, o.Gt); rnd(o64.GtT, o.GtT);
+            rnd(o64.Et, o.Et); rnd(o64.EtT, o.EtT);
+            if (opt.pcg_form == 1) {
+                // B is formed from the FP64 factor and rounded once to FP32, so its entries
+                // carry only their final rounding
+                rnd(o64.BW, o.BW);
+                transpose<TO>(o.BW.p, o.BW.ld, o.BWT.p, o.BWT.ld, n + m1, m2, s);
             }
+            wait_stream();
+            PCG_CK(cudaGetLastError());
+            o.factored = true;
+            return;
+        } else {
+        const double rel = 1e-13, warn = 1e-6;
+        chol_inv_prepare<TO, double>();
+        if (!o.px) {
+            alloc_op_vectors(o);
+            o.CW.p = C.p; o.CW.rows = m2; o.CW.cols = n; o.CW.ld = C.ld;
+            o.CWT.p = CT.p; o.CWT.rows = n; o.CWT.cols = m2; o.CWT.ld = CT.ld;
         }
         // scratch of the factorization (freed at the end)
         TO *Hw = nullptr, *Aw = nullptr, *G = nullptr, *S = nullptr;
@@ -513,7 +569,7 @@ public:
         PCG_CK(cudaMemsetAsync(o.WH.p, 0, (size_t)n * o.WH.ld * sizeof(TO), s));
         convert2d<double, TO>(H.p, H.ld, Hw, ldn, n, n, s);
         PCG_CK(cudaMemsetAsync(d_info, 0, 8 * sizeof(int), s));
-        chol_inv<TO, double>(Hw, ldn, o.WH.p, o.WH.ld, n, 0, rel, d_info, s, diag0);
+        chol_inv<TO, double>(Hw, ldn, o.WH.p, o.WH.ld, n, 0, rel, d_info, s, diag0, warn, d_info + 1);
         transpose<TO>(o.WH.p, o.WH.ld, o.WHT.p, o.WHT.ld, n, n, s);
         if (m1) {
             galloc(&Aw, (size_t)m1 * ldn);
@@ -535,7 +591,7 @@ public:
             h.B = G; h.sbk = 1; h.sbj = ldn;
             h.C = S; h.ldc = ldm; h.alpha = TO(1); h.beta = TO(0); h.lower_out = 1;
             gemm<TO>(h, s);
-            chol_inv<TO, double>(S, ldm, o.WS.p, o.WS.ld, m1, 0, rel, d_info + 2, s, diag0);
+            chol_inv<TO, double>(S, ldm, o.WS.p, o.WS.ld, m1, 0, rel, d_info + 2, s, diag0, warn, d_info + 3);
             // Gt = L_S^{-1} G
             GemmArgs<TO> k{};
             k.M = m1; k.N = n; k.K = m1;
@@ -555,14 +611,25 @@ public:
             gemm<TO>(e, s);
             transpose<TO>(o.Et.p, o.Et.ld, o.EtT.p, o.EtT.ld, m1, n, s);
         }
-        if (opt.pcg_form == 1 && !is64) {
-            // B is formed from the FP64 factor and rounded once to FP32, so its entries
-            // carry only their final rounding (an FP32 product over n terms of the FP32
-            // inverse factor would add about sqrt(n) u32 cond(R) relative error)
-            factor_op<double>();
-            convert2d<double, TO>(o64.BW.p, o64.BW.ld, o.BW.p, o.BW.ld, n + m1, m2, s);
-            transpose<TO>(o.BW.p, o.BW.ld, o.BWT.p, o.BWT.ld, n + m1, m2, s);
-        } else if (opt.pcg_form == 1) {
+        if (o.M0.p) {
+            // M0 = R^{-1} R^{-T} - Et' Et = H^{-1} - H^{-1} A' (A H^{-1} A')^{-1} A H^{-1}
+            // (opA(i,k) = WH[k,i], zero for k < i; opB(k,j) = WH[k,j], zero for k < j)
+            GemmArgs<TO> g{};
+            g.M = n; g.N = n; g.K = n;
+            g.A = o.WH.p; g.sai = 1; g.sak = o.WH.ld; g.a_tri = TRI_UPPER;
+            g.B = o.WH.p; g.sbk = o.WH.ld; g.sbj = 1; g.b_tri = TRI_LOWER;
+            g.C = o.M0.p; g.ldc = o.M0.ld; g.alpha = TO(1); g.beta = TO(0);
+            gemm<TO>(g, s);
+            if (m1) {
+                GemmArgs<TO> h{};
+                h.M = n; h.N = n; h.K = m1;
+                h.A = o.Et.p; h.sai = 1; h.sak = o.Et.ld;
+                h.B = o.Et.p; h.sbk = o.Et.ld; h.sbj = 1;
+                h.C = o.M0.p; h.ldc = o.M0.ld; h.alpha = TO(-1); h.beta = TO(1);
+                gemm<TO>(h, s);
+            }
+        }
+        if (opt.pcg_form == 1) {
             // B = L^{-1}[C'; 0]: B1 = R^{-T} C' (n x m2), B2 = Et C' (m1 x m2), and B'
             GemmArgs<TO> b1{};
             b1.M = n; b1.N = m2; b1.K = n;
@@ -589,27 +656,25 @@ public:
         PCG_CK(cudaGetLastError());
         if (h_info[0] != 0) throw QpError{QP_ENOTCONVEX};
         if (h_info[2] != 0) throw QpError{QP_ESINGULAR};
+        fp32_pivot_warn = (h_info[1] != 0) || (h_info[3] != 0);
         o.factored = true;
+        }
     }
 
     void factor() {
         if (factored) return;
         PCG_CK(cudaEventRecord(evA, s));
-        if (f64) {
-            factor_op<double>();
-        } else {
-            try {
-                factor_op<float>();
-            } catch (const QpError& e) {
-                // A pivot of the FP32 factor of H or of A H^{-1} A' fell below FP32
-                // resolution relative to its diagonal (ill-conditioned H or F_H): with
-                // mixed_fallback the QP is factored and solved in FP64, which decides
-                // whether the matrix is really singular or indefinite.
-                if (!((e.code == QP_ESINGULAR || e.code == QP_ENOTCONVEX) && allow_pc64)) throw;
-                if (verbose) std::fprintf(stderr, "  FP32 K0 factor failed (%d): FP64 from the start\n", e.code);
-                factor_op<double>();
+        factor_op<double>();
+        if (!f64) {
+            if (fp32_pivot_warn && allow_pc64) {
+                // A pivot of H or of A H^{-1} A' is below FP32 resolution relative to its
+                // diagonal (ill-conditioned H or F_H): with mixed_fallback the QP is solved
+                // with the FP64 operator from the start.
+                if (verbose) std::fprintf(stderr, "  K0 pivots below FP32 resolution: FP64 from the start\n");
                 all64 = true;
                 use64 = pc64 = true;
+            } else {
+                factor_op<float>();
             }
         }
         const int pc = resolve_pc(opt.precond, n, m1);
@@ -623,6 +688,12 @@ public:
         stats.t_factor_ms = ms;
         factored = true;
     }
+
+    // The persistent kernel applies an FP32 P_H factor as one symmetric product
+    // P~^{-1} = W'W (formed each IPM iteration, m2^3 flops at FP32 rates) and an FP64
+    // one as its two triangles W, then W' (one more phase, no FP64 product).
+    template <typename TP>
+    static constexpr bool ph_one_phase() { return std::is_same<TP, float>::value; }
 
     // T = C H^{-1} C' = (C R^{-1})(C R^{-1})' (exact) or C diag(H)^{-1} C' (diag),
     // once per QP, from the operator factor of the same precision.
@@ -638,10 +709,8 @@ public:
             P.WPl.alloc(arena, m2, m2);
             P.WPu.alloc(arena, m2, m2);
             P.sg = vec<TP>(m2); P.rs = vec<TP>(m2); P.pv = vec<TP>(m2); P.Dp = vec<TP>(m2);
-            const size_t ncp = std::max(1, (m2 + Chunk<TP>::n - 1) / Chunk<TP>::n);
-            P.ldV = m2;   // chunk-major partials: plane stride = m2
-            P.PV = arena.alloc<TP>((size_t)m2 * ncp);
-            P.PZ = arena.alloc<TP>((size_t)m2 * ncp);
+            P.oV[0] = vec<TP>(m2); P.oV[1] = vec<TP>(m2);
+            if (ph_one_phase<TP>()) P.PI.alloc(arena, m2, m2);
             chol_inv_prepare<TP, TP>();
         }
         TP* Bp = nullptr;
@@ -650,27 +719,54 @@ public:
             cudaGetLastError();
             throw NoMem{};
         }
-        if (kind == QP_PC_PH_EXACT) {
-            GemmArgs<TP> g{};
-            g.M = m2; g.N = n; g.K = n;
-            g.A = o.CW.p; g.sai = o.CW.ld; g.sak = 1;
-            g.B = o.WH.p; g.sbk = 1; g.sbj = o.WH.ld; g.b_tri = TRI_UPPER;
-            g.C = Bp; g.ldc = ldb; g.alpha = TP(1); g.beta = TP(0);
-            gemm<TP>(g, s);
-        } else {
-            double* hs = stage[3];
-            diag_rsqrt_kernel<<<vec_grid(n), kVecThreads, 0, s>>>(n, H.p, H.ld, hs);
-            convert2d<double, TP>(C.p, C.ld, Bp, ldb, m2, n, s, hs);
+        bool tc = false;
+        if constexpr (std::is_same<TP, float>::value) {
+            // FP32: both products on the tensor cores (FP32-accurate 3xTF32 splits)
+            float* sc = tc_scratch(tc_scratch_floats(n, m2));
+            float *ch = sc, *cl = ch + (size_t)m2 * ldb, *wh = cl + (size_t)m2 * ldb, *wl = wh + (size_t)n * ldb;
+            PCG_CK(cudaMemsetAsync(d_tcerr, 0, sizeof(int), s));
+            tc = true;
+            if (kind == QP_PC_PH_EXACT) {
+                // B = C R^{-1} = C WH': (B)_ij = sum_k C_ik WH_jk
+                tc_split(o.CW.p, o.CW.ld, m2, n, ch, cl, ldb, s);
+                tc_split(o.WH.p, o.WH.ld, n, n, wh, wl, ldb, s);
+                tc = tc_gemm(m2, n, n, 1.0f, ch, cl, ldb, wh, wl, ldb, 0.0f, Bp, ldb, true, false, d_tcerr, s);
+            } else {
+                double* hs = stage[3];
+                diag_rsqrt_kernel<<<vec_grid(n), kVecThreads, 0, s>>>(n, H.p, H.ld, hs);
+                convert2d<double, TP>(C.p, C.ld, Bp, ldb, m2, n, s, hs);
+            }
+            if (tc) {
+                // T = B B' (lower tiles)
+                tc_split(Bp, ldb, m2, n, ch, cl, ldb, s);
+                tc = tc_gemm(m2, m2, n, 1.0f, ch, cl, ldb, ch, cl, ldb, 0.0f, P.Tm.p, P.Tm.ld, true, true, d_tcerr, s);
+            }
+            if (!tc) cudaGetLastError();
         }
-        GemmArgs<TP> h{};
-        h.M = m2; h.N = m2; h.K = n;
-        h.A = Bp; h.sai = ldb; h.sak = 1;
-        h.B = Bp; h.sbk = 1; h.sbj = ldb;
-        h.C = P.Tm.p; h.ldc = P.Tm.ld; h.alpha = TP(1); h.beta = TP(0); h.lower_out = 1;
-        gemm<TP>(h, s);
+        if (!tc) {
+            if (kind == QP_PC_PH_EXACT) {
+                GemmArgs<TP> g{};
+                g.M = m2; g.N = n; g.K = n;
+                g.A = o.CW.p; g.sai = o.CW.ld; g.sak = 1;
+                g.B = o.WH.p; g.sbk = 1; g.sbj = o.WH.ld; g.b_tri = TRI_UPPER;
+                g.C = Bp; g.ldc = ldb; g.alpha = TP(1); g.beta = TP(0);
+                gemm<TP>(g, s);
+            } else {
+                double* hs = stage[3];
+                diag_rsqrt_kernel<<<vec_grid(n), kVecThreads, 0, s>>>(n, H.p, H.ld, hs);
+                convert2d<double, TP>(C.p, C.ld, Bp, ldb, m2, n, s, hs);
+            }
+            GemmArgs<TP> h{};
+            h.M = m2; h.N = m2; h.K = n;
+            h.A = Bp; h.sai = ldb; h.sak = 1;
+            h.B = Bp; h.sbk = 1; h.sbj = ldb;
+            h.C = P.Tm.p; h.ldc = P.Tm.ld; h.alpha = TP(1); h.beta = TP(0); h.lower_out = 1;
+            gemm<TP>(h, s);
+        }
         cudaFreeAsync(Bp, s);
         wait_stream();
         PCG_CK(cudaGetLastError());
+        if (std::is_same<TP, float>::value) tc_check();
         P.t_kind = kind;
     }
 
@@ -692,13 +788,43 @@ public:
             build_scaled_ph_kernel<TP><<<304 * 4, 256, 0, s>>>(P.Tm.p, P.Tm.ld, P.Dp, P.Pm.p, P.Pm.ld, P.sg, m2, shift);
             PCG_CK(cudaMemsetAsync(P.WPl.p, 0, (size_t)m2 * P.WPl.ld * sizeof(TP), s));
             PCG_CK(cudaMemsetAsync(d_info + 4, 0, sizeof(int), s));
-            chol_inv<TP, TP>(P.Pm.p, P.Pm.ld, P.WPl.p, P.WPl.ld, m2, 1, floor, d_info + 4, s);
+            if constexpr (std::is_same<TP, float>::value) {
+                PCG_CK(cudaMemsetAsync(d_tcerr, 0, sizeof(int), s));
+                chol_inv_tc<float>(P.Pm.p, P.Pm.ld, P.WPl.p, P.WPl.ld, m2, 1, floor, d_info + 4, s,
+                                   tc_scratch(tc_scratch_floats(n, m2)), d_tcerr);
+            } else {
+                chol_inv<TP, TP>(P.Pm.p, P.Pm.ld, P.WPl.p, P.WPl.ld, m2, 1, floor, d_info + 4, s);
+            }
             PCG_CK(cudaMemcpyAsync(h_info + 4, d_info + 4, sizeof(int), cudaMemcpyDeviceToHost, s));
             sync_check();
             if (h_info[4] == 0) break;
             shift = (shift == 0.0) ? (is64 ? 1e-10 : 1e-4) : shift * 10.0;
         }
         transpose<TP>(P.WPl.p, P.WPl.ld, P.WPu.p, P.WPu.ld, m2, m2, s);
+        bool pi_tc = false;
+        if constexpr (std::is_same<TP, float>::value) {
+            if (P.PI.p) {
+                // P~^{-1} = W'W = U U' with U = W' (upper, stored as WPu): tensor cores
+                const long long ldm = pad_ld(m2);
+                float* sc = tc_scratch(tc_scratch_floats(n, m2));
+                float *uh = sc, *ul = sc + (size_t)m2 * ldm;
+                tc_split(P.WPu.p, P.WPu.ld, m2, m2, uh, ul, ldm, s);
+                pi_tc = tc_gemm(m2, m2, m2, 1.0f, uh, ul, ldm, uh, ul, ldm, 0.0f, P.PI.p, P.PI.ld, true, false,
+                                d_tcerr, s);
+                if (!pi_tc) cudaGetLastError();
+            }
+        }
+        if (P.PI.p && !pi_tc) {
+            // P~^{-1} = W' W (W = L^{-1} lower): opA(i,k) = W[k,i], zero for k < i;
+            // opB(k,j) = W[k,j], zero for k < j
+            GemmArgs<TP> g{};
+            g.M = m2; g.N = m2; g.K = m2;
+            g.A = P.WPl.p; g.sai = 1; g.sak = P.WPl.ld; g.a_tri = TRI_UPPER;
+            g.B = P.WPl.p; g.sbk = P.WPl.ld; g.sbj = 1; g.b_tri = TRI_LOWER;
+            g.C = P.PI.p; g.ldc = P.PI.ld; g.alpha = TP(1); g.beta = TP(0);
+            gemm<TP>(g, s);
+        }
+        if (std::is_same<TP, float>::value) tc_check();
         P.shift = shift;
         if (verbose && shift > 0) std::fprintf(stderr, "  P_H shift %.1e\n", shift);
         return shift;
@@ -826,6 +952,149 @@ public:
         return ge;
     }
 
+    // ------------------------------------------------- persistent PCG kernel
+    // Phases of the persistent kernel for the handle's pcg_form and preconditioner
+    // kind, with every block's rows (whole rows, balanced by chunk count) in tbl.
+    struct FusedPlan {
+        Phase ph[kMaxPhases];
+        int nop = 0, npc = 0;
+        size_t xs_elems_o = 0, xs_elems_p = 0;   // staged-vector length in TO / TP elements
+        size_t spart_bytes = 0;
+        std::vector<int2> tbl;
+    };
+    int2* d_tbl = nullptr;                 // device copy of the block tables (kMaxPhases x (1024 + 1))
+    std::vector<int2> h_tbl_cur;           // what d_tbl holds
+    static constexpr int kTblStride = 1025;
+
+    static Part mk_part(const void* M, long long ld, int r0, int r1, int cols, int tri, int xoff) {
+        Part p;
+        p.M = M; p.ld = ld; p.r0 = r0; p.r1 = r1; p.cols = cols; p.tri = tri; p.xoff = xoff;
+        return p;
+    }
+    static int padc(int v, int ch) { return (v + ch - 1) / ch * ch; }
+
+    static int slot_bytes_for(int grid) { return grid > kMaxClusterBlocks ? kBigSlotBytes : kSmallSlotBytes; }
+
+    template <typename TO, typename TP>
+    FusedPlan plan_fused(int kind, int grid) {
+        Op<TO>& o = op<TO>();
+        Pc<TP>& P = pcd<TP>();
+        const int sb = slot_bytes_for(grid);
+        const int CHO = sb / (int)sizeof(TO), CHP = sb / (int)sizeof(TP);
+        auto p32 = [](int v) { return (v + 31) / 32 * 32; };   // staged vectors: the matrices' leading dimension
+        FusedPlan F;
+        auto phase = [&](std::initializer_list<Part> parts, int rows) {
+            Phase ph{};
+            ph.np = 0;
+            for (const Part& q : parts) ph.p[ph.np++] = q;
+            ph.rows = rows;
+            ph.in_s2 = 1.0f;
+            return ph;
+        };
+        auto input = [&](Phase& ph, int len1, int off2, int len2, float s2, int pad) {
+            ph.in_len1 = len1; ph.in_off2 = off2; ph.in_len2 = len2; ph.in_s2 = s2; ph.in_pad = pad;
+        };
+        const int form = opt.pcg_form;
+        if (form == 1) {
+            F.ph[0] = phase({mk_part(o.BW.p, o.BW.ld, 0, n + m1, m2, TRI_NONE, 0)}, n + m1);
+            F.ph[1] = phase({mk_part(o.BWT.p, o.BWT.ld, 0, m2, n + m1, TRI_NONE, 0)}, m2);
+            input(F.ph[1], n, n, m1, -1.0f, p32(n + m1));
+            F.nop = 2;
+        } else if (form == 2) {
+            F.ph[0] = phase({mk_part(o.CWT.p, o.CWT.ld, 0, n, m2, TRI_NONE, 0)}, n);
+            if (m1) {
+                F.ph[1] = phase({mk_part(o.WH.p, o.WH.ld, 0, n, n, TRI_LOWER, 0),
+                                 mk_part(o.Et.p, o.Et.ld, n, n + m1, n, TRI_NONE, 0)}, n + m1);
+                F.ph[2] = phase({mk_part(o.WHT.p, o.WHT.ld, 0, n, n, TRI_UPPER, 0),
+                                 mk_part(o.EtT.p, o.EtT.ld, 0, n, m1, TRI_NONE, p32(n))}, n);
+                input(F.ph[2], n, p32(n), m1, -1.0f, p32(n) + p32(m1));
+            } else {
+                F.ph[1] = phase({mk_part(o.WH.p, o.WH.ld, 0, n, n, TRI_LOWER, 0)}, n);
+                F.ph[2] = phase({mk_part(o.WHT.p, o.WHT.ld, 0, n, n, TRI_UPPER, 0)}, n);
+                input(F.ph[2], n, 0, 0, 1.0f, p32(n));
+            }
+            input(F.ph[1], n, 0, 0, 1.0f, p32(n));
+            F.ph[3] = phase({mk_part(o.CW.p, o.CW.ld, 0, m2, n, TRI_NONE, 0)}, m2);
+            input(F.ph[3], n, 0, 0, 1.0f, p32(n));
+            F.nop = 4;
+        } else {
+            F.ph[0] = phase({mk_part(o.CWT.p, o.CWT.ld, 0, n, m2, TRI_NONE, 0)}, n);
+            F.ph[1] = phase({mk_part(o.M0.p, o.M0.ld, 0, n, n, TRI_NONE, 0)}, n);
+            input(F.ph[1], n, 0, 0, 1.0f, p32(n));
+            F.ph[2] = phase({mk_part(o.CW.p, o.CW.ld, 0, m2, n, TRI_NONE, 0)}, m2);
+            input(F.ph[2], n, 0, 0, 1.0f, p32(n));
+            F.nop = 3;
+        }
+        if (kind == PC_H_K) {
+            if (P.PI.p) {
+                F.ph[F.nop] = phase({mk_part(P.PI.p, P.PI.ld, 0, m2, m2, TRI_NONE, 0)}, m2);
+                F.npc = 1;
+            } else {
+                F.ph[F.nop] = phase({mk_part(P.WPl.p, P.WPl.ld, 0, m2, m2, TRI_LOWER, 0)}, m2);
+                F.ph[F.nop + 1] = phase({mk_part(P.WPu.p, P.WPu.ld, 0, m2, m2, TRI_UPPER, 0)}, m2);
+                input(F.ph[F.nop + 1], m2, 0, 0, 1.0f, p32(m2));
+                F.npc = 2;
+            }
+        }
+        // the first phase's input is p (m2, padded); the P_H phases' is Sg r
+        F.xs_elems_o = p32(m2);
+        F.xs_elems_p = p32(m2);
+        F.tbl.assign((size_t)(F.nop + F.npc) * (grid + 1), int2{0, 0});
+        for (int k = 0; k < F.nop + F.npc; ++k) {
+            Phase& ph = F.ph[k];
+            const bool isP = k >= F.nop;
+            const int CH = isP ? CHP : CHO;
+            const size_t es = isP ? sizeof(TP) : sizeof(TO);
+            if (k > 0 && k != F.nop) {
+                if (isP) F.xs_elems_p = std::max(F.xs_elems_p, (size_t)ph.in_pad);
+                else F.xs_elems_o = std::max(F.xs_elems_o, (size_t)ph.in_pad);
+            }
+            std::vector<int> pre(ph.rows + 1, 0);
+            int ncmax = 1;
+            for (int r = 0; r < ph.rows; ++r) {
+                const int it = row_items(ph, CH, r);
+                ncmax = std::max(ncmax, it);
+                pre[r + 1] = pre[r] + it;
+            }
+            ph.ncmax = ncmax;
+            ph.tbl = k * (grid + 1);
+            const long long total = pre[ph.rows];
+            int maxrows = 0;
+            for (int b = 0; b <= grid; ++b) {
+                const long long tgt = (total * b + grid / 2) / grid;
+                const int r = (b == grid) ? ph.rows
+                                          : (int)(std::lower_bound(pre.begin(), pre.end(), (int)tgt) - pre.begin());
+                F.tbl[(size_t)ph.tbl + b] = int2{r, pre[r]};
+                if (b > 0) maxrows = std::max(maxrows, r - F.tbl[(size_t)ph.tbl + b - 1].x);
+            }
+            F.spart_bytes = std::max(F.spart_bytes, (size_t)maxrows * ncmax * es);
+            // every part's stored row (leading dimension) must lie inside the staged vector
+            for (int q = 0; q < ph.np; ++q) {
+                const size_t need = (size_t)ph.p[q].xoff + (size_t)ph.p[q].ld;
+                if (isP) F.xs_elems_p = std::max(F.xs_elems_p, need);
+                else F.xs_elems_o = std::max(F.xs_elems_o, need);
+            }
+        }
+        return F;
+    }
+
+    template <typename TO, typename TP>
+    size_t fused_xs_bytes(const FusedPlan& F) const {
+        const size_t b = std::max(F.xs_elems_o * sizeof(TO), F.xs_elems_p * sizeof(TP));
+        return (b + 15) / 16 * 16;
+    }
+
+    // Ring depth: as deep as the block's shared-memory limit allows after the staged
+    // vector, the three m2-vector caches and the per-row partials (at most kMaxSlots).
+    template <typename TO, typename TP>
+    int fused_slots(const FusedPlan& F, int slot_bytes) const {
+        const size_t off = fused_ring_offset(fused_spart_offset<TO>(fused_xs_bytes<TO, TP>(F), m2), F.spart_bytes);
+        const size_t lim = fused_smem_limit();
+        const size_t per = slot_bytes + 2 * sizeof(uint64_t) + sizeof(int);
+        if (off + 16 + per > lim) return 0;
+        return (int)std::min<size_t>(kMaxSlots, (lim - off - 16) / per);
+    }
+
     // The persistent cooperative PCG kernel: one launch runs the whole solve from
     // the pcg_init state (x = 0, r = rhs, p = z0); the final state ends in hst[0].
     // Small QPs (a grid of at most kMaxClusterBlocks) run 256-thread blocks, two per
@@ -845,38 +1114,52 @@ public:
     void launch_fused_nt(int grid, int sms) {
         Op<TO>& o = op<TO>();
         Pc<TP>& P = pcd<TP>();
+        FusedPlan F = plan_fused<TO, TP>(PC, grid);
+        const bool same = F.tbl.size() == h_tbl_cur.size() &&
+                          std::memcmp(F.tbl.data(), h_tbl_cur.data(), F.tbl.size() * sizeof(int2)) == 0;
+        if (!same) {
+            if (F.tbl.size() > (size_t)kMaxPhases * kTblStride) throw QpError{QP_EINVAL};
+            h_tbl_cur = F.tbl;
+            PCG_CK(cudaMemcpyAsync(d_tbl, h_tbl_cur.data(), h_tbl_cur.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+        }
         FusedArgs<TO, TP> fa{};
         fa.n = n; fa.m1 = m1; fa.m2 = m2;
-        fa.CWT = o.CWT.p; fa.ldCWT = o.CWT.ld; fa.WH = o.WH.p; fa.ldWH = o.WH.ld;
-        fa.Et = o.Et.p; fa.ldEt = o.Et.ld; fa.EtT = o.EtT.p; fa.ldEtT = o.EtT.ld;
-        fa.wform = (opt.pcg_form == 1) ? 1 : 0;
-        fa.BW = o.BW.p; fa.ldBW = o.BW.ld; fa.BWT = o.BWT.p; fa.ldBWT = o.BWT.ld; fa.PW = o.PW; fa.ldPW = o.ldW;
-        fa.WHT = o.WHT.p; fa.ldWHT = o.WHT.ld; fa.CW = o.CW.p; fa.ldCW = o.CW.ld;
-        fa.WPl = P.WPl.p; fa.WPu = P.WPu.p; fa.ldWP = P.WPl.ld; fa.sg = P.sg;
+        for (int k = 0; k < F.nop + F.npc; ++k) fa.ph[k] = F.ph[k];
+        fa.nop = F.nop; fa.npc = F.npc;
+        fa.tbl = d_tbl;
+        if (opt.pcg_form == 1) {
+            fa.out[0] = o.oZ; fa.out[1] = o.oW;
+        } else if (opt.pcg_form == 2) {
+            fa.out[0] = o.oU; fa.out[1] = o.oZ; fa.out[2] = o.oY; fa.out[3] = o.oW;
+        } else {
+            fa.out[0] = o.oU; fa.out[1] = o.oY; fa.out[2] = o.oW;
+        }
+        fa.outP[0] = P.oV[0]; fa.outP[1] = P.oV[1];
+        fa.sg = P.sg;
         fa.D = o.pD; fa.Dinv = o.pDinv; fa.x = o.px;
-        fa.r0 = o.pr; fa.r1 = o.pr1; fa.p0 = o.pp; fa.p1 = o.pp1;
-        fa.PU = o.PU; fa.PZ1 = o.PZ1; fa.PZ2 = o.PZ2; fa.PT = o.PT; fa.PY = o.PY; fa.PQ = o.PQ;
-        fa.PV = P.PV; fa.PZ = P.PZ;
-        fa.ldU = o.ldU; fa.ldZ1 = o.ldZ1; fa.ldZ2 = o.ldZ2; fa.ldT = o.ldT; fa.ldY = o.ldY; fa.ldQ = o.ldQ;
-        fa.ldV = P.ldV; fa.ldZ = P.ldV;
+        fa.r_in = o.pr; fa.p_in = o.pp;
         fa.st = st; fa.bar = bar;
         fa.tstamp = phase_times ? tstamp : nullptr;
         fa.leave_early = leave_early ? 1 : 0;
         auto kern = pcg_fused_kernel<TO, TP, PC, NT>;
-        const size_t xsb = fused_xs_bytes<TO, TP>();
-        fa.xs_bytes = xsb;
-        fa.ring_off = fused_ring_offset<TO>(xsb, m2);
+        fa.xs_bytes = fused_xs_bytes<TO, TP>(F);
+        fa.spart_off = fused_spart_offset<TO>(fa.xs_bytes, m2);
+        fa.ring_off = fused_ring_offset(fa.spart_off, F.spart_bytes);
         int per_sm = 0;
         // A QP whose grid covers most of the GPU takes the deepest ring that fits; a
         // small one (batched with others) a shallow ring, so that the blocks of several
         // QPs share an SM.
-        fa.slots = fused_slots<TO, TP, NT>();
-        if (2 * grid < sms) fa.slots = std::min(fa.slots, Blk<NT>::small_slots);
-        if (fa.slots < Blk<NT>::warps) throw QpError{QP_ENOMEM};
-        const size_t smem = fused_smem_bytes(fa.ring_off, fa.slots);
+        fa.slot_bytes = slot_bytes_for(grid);
+        fa.slots = fused_slots<TO, TP>(F, fa.slot_bytes);
+        if (2 * grid < sms) fa.slots = std::min(fa.slots, kSmallRingSlots);
+        if (fa.slots < min_slots(grid)) {
+            if (verbose) std::fprintf(stderr, "  persistent PCG: %d ring slots of %d bytes do not fit\n", fa.slots, fa.slot_bytes);
+            throw QpError{QP_ENOMEM};
+        }
+        const size_t smem = fused_smem_bytes(fa.ring_off, fa.slots, fa.slot_bytes);
         // Kernel attributes are shared by every thread of the process: set them once
-        // (the dynamic shared-memory limit to what fused_slots() sizes the ring for;
-        // the launch itself uses only `smem`), never per call.
+        // (the dynamic shared-memory limit to the block's maximum; the launch itself
+        // uses only `smem`), never per call.
         static const cudaError_t attr_ok = [&]() {
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                  (int)fused_smem_limit());
@@ -885,7 +1168,10 @@ public:
         }();
         PCG_CK(attr_ok);
         PCG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
-        if (per_sm < 1) throw QpError{QP_ENOMEM};
+        if (per_sm < 1) {
+            if (verbose) std::fprintf(stderr, "  persistent PCG: no block fits with %zu bytes of shared memory\n", smem);
+            throw QpError{QP_ENOMEM};
+        }
         PCG_CK(cudaMemsetAsync(bar, 0, sizeof(GridBar), s));
         // A grid of at most kMaxClusterBlocks blocks is launched as one thread-block
         // cluster: the hardware schedules the blocks of a cluster together, which is all
@@ -920,7 +1206,9 @@ public:
             void* args[] = {(void*)&fa};
             PCG_CK(cudaLaunchCooperativeKernel((const void*)kern, grid, NT, args, smem, s));
         }
+        last_fused_grid = grid;
     }
+    int last_fused_grid = 0;
 
     template <typename TO, typename TP>
     void pcg_run_fused(int kind) {
@@ -928,12 +1216,13 @@ public:
         else if (kind == PC_H_K) launch_fused<TO, TP, PC_H_K>();
         else launch_fused<TO, TP, PC_NONE_K>();
         PCG_CK(cudaMemcpyAsync(&hst[0], st, sizeof(PcgState), cudaMemcpyDeviceToHost, s));
-        PCG_CK(cudaMemcpyAsync(h_info + 6, &bar->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+        PCG_CK(cudaMemcpyAsync(h_info + 6, &bar->count, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
         sync_check();
-        if (h_info[6] != 0) throw QpError{QP_ETIMEOUT};
+        if ((unsigned)h_info[6] & kBarErr) throw QpError{QP_ETIMEOUT};
         if (phase_times && hst[0].iter >= 4) {
-            unsigned long long t[4 * 32];
-            PCG_CK(cudaMemcpyAsync(t, tstamp, sizeof(t), cudaMemcpyDeviceToHost, s));
+            const int G = last_fused_grid;
+            std::vector<unsigned long long> t(128 + 8 * (size_t)G);
+            PCG_CK(cudaMemcpyAsync(t.data(), tstamp, t.size() * 8, cudaMemcpyDeviceToHost, s));
             wait_stream();
             std::fprintf(stderr, "phase marks (us from iteration start):");
             for (int i = 1; i < 4; ++i) {
@@ -941,52 +1230,45 @@ public:
                 for (int ph = 1; ph < 32; ++ph)
                     if (t[i * 32 + ph] > t[i * 32]) std::fprintf(stderr, " m%d=%.1f", ph, (t[i * 32 + ph] - t[i * 32]) * 1e-3);
             }
+            std::fprintf(stderr, "\n  iteration 2, phase ends over blocks (us from iteration start): ");
+            for (int ph = 0; ph < 8; ++ph) {
+                unsigned long long lo = ~0ull, hi = 0;
+                for (int b = 0; b < G; ++b) {
+                    const unsigned long long v = t[128 + (size_t)ph * G + b];
+                    if (!v) continue;
+                    lo = std::min(lo, v); hi = std::max(hi, v);
+                }
+                if (hi) std::fprintf(stderr, " ph%d [%.1f, %.1f]", ph, (lo - t[2 * 32]) * 1e-3, (hi - t[2 * 32]) * 1e-3);
+            }
             std::fprintf(stderr, "\n");
-            PCG_CK(cudaMemsetAsync(tstamp, 0, sizeof(t), s));
+            PCG_CK(cudaMemsetAsync(tstamp, 0, t.size() * 8, s));
         }
     }
 
-    // Shared memory of the persistent kernel: one staged vector, three m2-vectors,
-    // and a ring of 4 KB chunk slots as deep as the rest of the block's limit allows
-    // (at most three slots per consumer warp).  With fewer slots than consumer warps the per-phase kernels
-    // are used instead.
+    // Shared memory of the persistent kernel: the opt-in limit of a block, less the
+    // kernel's static shared memory (scalars, below 1 KB).
     static size_t fused_smem_limit() {
         static const size_t lim = []() {
             int d = 0, optin = 0;
             cudaGetDevice(&d);
             cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, d);
             if (optin <= 0) optin = 227 * 1024;
-            return (size_t)optin - 1024;   // static shared memory of the kernel (scalars) below 1 KB
+            return (size_t)optin - 1024;
         }();
         return lim;
     }
-    // staged vector: p (m2), u or y (n), z1 and z2 side by side (n + m1), or r for P_H (m2 in TP),
-    // each padded to whole chunks
     template <typename TO, typename TP>
-    size_t fused_xs_bytes() const {
-        const size_t CO = Chunk<TO>::n, CP = Chunk<TP>::n;
-        auto padto = [](size_t v, size_t c) { return (v + c - 1) / c * c; };
-        const size_t elems = std::max(std::max(padto(n, CO), padto(m2, CO)), padto(n, CO) + padto(std::max(m1, 1), CO));
-        const size_t xsb = std::max(elems * sizeof(TO), padto(m2, CP) * sizeof(TP));
-        return (xsb + 15) / 16 * 16;
-    }
-    template <typename TO, typename TP, int NT>
-    int fused_slots() const {
-        const size_t off = fused_ring_offset<TO>(fused_xs_bytes<TO, TP>(), m2);
-        const size_t lim = fused_smem_limit();
-        const size_t per = kSlotBytes + 2 * sizeof(uint64_t) + sizeof(int);
-        if (off + 16 + per > lim) return 0;
-        const int sl = (int)std::min<size_t>(Blk<NT>::max_slots, (lim - off - 16) / per);
-        return sl / Blk<NT>::warps * Blk<NT>::warps;   // the ring protocol wants a multiple of the consumer warps
-    }
-    template <typename TO, typename TP>
-    bool fused_fits() const {
+    bool fused_fits(int kind) {
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (fused_grid(sms) <= kMaxClusterBlocks) return fused_slots<TO, TP, kSmallBlock>() >= Blk<kSmallBlock>::warps;
-        return fused_slots<TO, TP, kBigBlock>() >= Blk<kBigBlock>::warps;
+        const int grid = fused_grid(sms);
+        const FusedPlan F = plan_fused<TO, TP>(kind, grid);
+        return fused_slots<TO, TP>(F, slot_bytes_for(grid)) >= min_slots(grid);
     }
+    // Fewest ring slots the persistent kernel runs with: 16 KB slots stream at the copy
+    // rate with a handful in flight; 4 KB slots need one per consumer warp.
+    static int min_slots(int grid) { return grid > kMaxClusterBlocks ? 6 : Blk<kSmallBlock>::warps; }
 
     bool use_fused() const { return opt.pcg_check_every >= 0; }
 
@@ -1009,7 +1291,7 @@ public:
     // pipelined one graph launch behind.
     template <typename TO, typename TP>
     void pcg_run(int kind, int maxit) {
-        if (use_fused() && fused_fits<TO, TP>()) {
+        if (use_fused() && fused_fits<TO, TP>(kind)) {
             pcg_run_fused<TO, TP>(kind);
             return;
         }
@@ -1113,7 +1395,7 @@ public:
     template <typename TO, typename TP>
     void time_pcg_t(int kind, int warmup, int iters, double* ms_out) {
         Op<TO>& o = op<TO>();
-        if (use_fused() && fused_fits<TO, TP>()) {
+        if (use_fused() && fused_fits<TO, TP>(kind)) {
             // warm-up solve, then a timed solve of `iters` iterations (tolerance 0:
             // no early stop); the timed region includes the start kernels.
             pcg_init<TO, TP>(kind, o.prhs, 0.0, std::max(1, warmup), 0);
@@ -1162,14 +1444,19 @@ public:
 
     // Algorithmic bytes of one PCG iteration (the per-iteration traffic of
     // Table tab:costs with dense operands): C' p and C y stream C twice; the K0
-    // solve streams the two triangles of R^{-1} and Gt twice; P_H streams the two
-    // triangles of its inverse factor; plus the vector traffic.
+    // solve streams M0 (pcg_form 0), or the two triangles of R^{-1} and Et twice
+    // (pcg_form 2 and the per-phase kernels), or B and B' replace all three
+    // (pcg_form 1); P_H streams P~^{-1} (FP32) or the two triangles of its inverse
+    // factor (FP64); plus the vector traffic.
     double bytes_per_iter(int pc) const {
         pc = resolve_pc(pc, n, m1);
         const double eo = use64 ? 8.0 : 4.0, ep = pc64 ? 8.0 : 4.0;
-        const double bo = (opt.pcg_form == 1 && use_fused()) ? 2.0 * (n + m1) * m2
-                                                            : 2.0 * m2 * n + (double)n * (n + 1) + 2.0 * m1 * n;
-        const double bp = pc_kind(pc) == PC_H_K ? (double)m2 * (m2 + 1) : 0.0;
+        const bool fused = use_fused();
+        double bo = 2.0 * m2 * n + (double)n * (n + 1) + 2.0 * m1 * n;   // C', the factor's triangles, C
+        if (fused && opt.pcg_form == 1) bo = 2.0 * (n + m1) * m2;         // B and B'
+        if (fused && opt.pcg_form == 0) bo = 2.0 * m2 * n + (double)n * n;   // C', M0, C
+        double bp = 0.0;
+        if (pc_kind(pc) == PC_H_K) bp = (fused && !pc64) ? (double)m2 * m2 : (double)m2 * (m2 + 1);
         const double vec_el = 12.0 * m2 + 8.0 * n + 4.0 * m1;
         return bo * eo + bp * ep + vec_el * eo;
     }

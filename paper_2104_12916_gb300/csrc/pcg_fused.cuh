@@ -1,35 +1,40 @@
 // pcg_fused.cuh -- the PCG hot loop (a6-a10) as one persistent cooperative kernel.
 //
 // One launch runs every iteration of one PCG solve on K_F dnu = r_nu.  An
-// iteration is a chain of row-major matrix-vector phases separated by grid
-// barriers: u = C' p; the forward solve with the K0 factor L (stored as its
-// inverse: z1 = R^{-T} u and z2 = -Et u together, Et = L_S^{-1} A H^{-1} the
-// (2,1) block of L^{-1}); the back solve y = R^{-1} z1 + Et' z2; q = D p + C y;
-// then for P_H the two triangles of the inverse factor of P~.
+// iteration is a short chain of row-major matrix-vector phases separated by
+// grid barriers.  With the default form (pcg_form 0):
+//   u = C' p;  y = M0 u with M0 = [K0^{-1}]_11 = R^{-1} R^{-T} - Et' Et, the
+//   (1,1) block of the inverse of the K0 factorization (the forward and the
+//   back solve of Sec. 5.2's second step in one product, formed once per QP);
+//   q = D p + C y;  and for P_H, v = P~^{-1} (Sg r) with P~^{-1} = W' W the
+//   inverse of the Jacobi-scaled P_H from its Cholesky factor W^{-1}.
+// pcg_form 2 keeps the two triangular solves with the stored inverse factor
+// ([R^{-T}; Et] u, then [R^{-1} | Et'] [z1; -z2]); pcg_form 1 applies
+// K_F through B = L^{-1}[C'; 0] (two phases).
 //
-// Layout of the work: a matrix is cut into chunks of 4 KB of one row (1024 FP32
-// or 512 FP64 elements).  Each block owns a contiguous range of the chunks of
-// every phase (rows next to each other in one chunk column).  The matrices do
-// not change during the solve, so their stream need not wait for the barriers:
-// a producer warp copies the block's chunks, phase after phase and iteration
-// after iteration, into a ring of shared-memory slots with bulk asynchronous
-// copies (cp.async.bulk, completion counted on one mbarrier per slot), running
-// ahead of the consumers by up to the ring's depth -- across the grid barriers,
-// where a kernel that only loads after the barrier leaves HBM idle.  The 15
-// consumer warps take the block's chunks in turn, dot them with the staged
-// vector and write one partial sum per chunk; the next phase, while staging its
-// input vector, adds a row's chunk partials in a fixed order and applies the
-// elementwise part of the method (D p, z1 + ..., the Jacobi scaling, the PCG
-// updates).  The PCG dot products (p'q, |r|^2, r'z) are summed by every block
-// over the whole vector in the same fixed order, so every block holds
-// bit-identical scalars without a reduction barrier.  Vectors read and written
-// in one phase (r, p) are double-buffered; each block writes only its own slice.
-//
-// Chunks that lie entirely outside a triangle are skipped (no copy, no
-// partial); inside a chunk, the zeros the triangle stores in memory are read.
+// Layout of the work.  A matrix is cut into chunks of one row of at most one
+// ring slot (16 KB for a QP spread over the GPU, 4 KB for a small one); chunks
+// that lie entirely outside a stored triangle are left out.  (Bulk copies of
+// 4 KB stream at about half the HBM rate of 16 KB ones: the copy engine's rate
+// per copy, not the ring depth, bounds them.)  Each block owns a contiguous range of whole rows of
+// every phase (balanced by chunk count on the host), so a row's result is
+// summed by one block in a fixed order and written once: the next phase stages
+// its input with one load per element.  The matrices do not change during the
+// solve, so their stream does not wait for the barriers: a producer warp
+// copies the block's chunks, phase after phase and iteration after iteration,
+// into a ring of shared-memory slots with bulk asynchronous copies
+// (cp.async.bulk, completion counted on one mbarrier per slot), running ahead
+// of the consumers by up to the ring's depth -- across the grid barriers, where
+// a kernel that only loaded after the barrier would leave HBM idle.  Consumer
+// warps dot the chunks with the staged vector and keep one partial per chunk
+// in shared memory; after the phase each owned row is summed in chunk order.
+// The PCG scalars (p'q, |r|^2, r'z) are summed by every block over the whole
+// vectors in the same fixed order, so every block holds bit-identical scalars
+// without a reduction barrier, and the vector updates are done redundantly in
+// shared memory (each block writes only its own slice of x).
 //
 // Every wait is bounded in time (kWaitNs on %globaltimer): a consumer that gives
-// up records QP_ETIMEOUT in the barrier word and every block returns at its next
+// up sets the error bit of the barrier word and every block returns at its next
 // grid barrier; the producer stops when the consumers stop (or its own wait
 // gives up) and then waits, again bounded, for the copies it has in flight.
 #pragma once
@@ -49,27 +54,74 @@ constexpr int kBigBlock = 512, kSmallBlock = 256;
 template <int NT> struct Blk {
     static constexpr int threads = NT - 32;            // consumer threads
     static constexpr int warps = threads / 32;         // consumer warps
-    static constexpr int max_slots = 3 * warps;        // ring depths are multiples of `warps`
-    static constexpr int small_slots = 2 * warps;      // ring of a QP that shares the GPU
 };
-constexpr int kSlotBytes = 4096;
+constexpr int kBigSlotBytes = 16384;              // ring slot of a QP spread over the GPU
+constexpr int kSmallSlotBytes = 4096;             // ring slot of a small QP (its rows are short)
+constexpr int kMaxSlots = 64;                     // two slots per producer lane at most
+constexpr int kSmallRingSlots = 14;               // ring of a QP whose grid covers a small part of the GPU
 constexpr int kMaxClusterBlocks = 16;             // grids up to this size launch as one cluster
+constexpr int kMaxPhases = 6;                     // operator phases (pcg_form 2: four) + P_H (one or two)
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s bound on any wait
+constexpr unsigned kBarErr = 0x40000000u;         // error bit of the barrier counter
 
+// Grid barrier word: a monotonic arrival counter (zeroed before each launch)
+// whose bit 30 records a failure anywhere, so one acquire load tells a polling
+// block both that the round is complete and whether to leave.
 struct GridBar {
-    unsigned int count;   // monotonic arrival counter (zeroed before each launch)
-    unsigned int gen;
-    int err;
-    int pad;
+    unsigned count;
+    unsigned pad[31];
 };
 
-// Accumulation type of the staging sums and PCG scalars inside the fused kernel:
+// Accumulation type of the chunk dots and PCG scalars inside the fused kernel:
 // the working precision itself.  (GB300's FP64 pipe issues two FMAs per clock per
 // SM, so an FP32 path must not touch FP64 arithmetic in its inner loops.)
 template <typename T> struct Acc { using type = T; };
 
-// Elements of one chunk for matrix element type T (one 4 KB slot).
-template <typename T> struct Chunk { static constexpr int n = kSlotBytes / (int)sizeof(T); };
+// One row-major matrix of a phase: it contributes to phase rows [r0, r1), its
+// columns are dotted with the staged vector from offset xoff, and chunks outside
+// its stored triangle (relative to its own rows, i = r - r0) are skipped.
+struct Part {
+    const void* M;
+    long long ld;     // row stride in elements (a multiple of 32: rows start 128-byte aligned)
+    int r0, r1;
+    int cols;
+    int tri;          // TRI_NONE, TRI_LOWER (row i: chunks up to i's), TRI_UPPER (from i's)
+    int xoff;
+};
+
+// A phase: up to two parts (stacked rows, or side by side on the same rows),
+// and how its input is staged from the previous phase's output:
+// xs[j] = out[j] (j < in_len1), xs[in_off2 + j] = in_s2 * out[in_len1 + j] (j < in_len2),
+// zeros elsewhere up to in_pad.
+struct Phase {
+    Part p[2];
+    int np;
+    int rows;
+    int ncmax;        // most chunks of one row (stride of the per-row partials)
+    int tbl;          // offset of this phase's (first row, first item) table: grid + 1 entries
+    int in_len1, in_off2, in_len2, in_pad;
+    float in_s2;
+};
+
+__host__ __device__ inline void part_chunks(const Part& P, int CH, int r, int& c0, int& c1) {
+    c0 = c1 = 0;
+    if (r < P.r0 || r >= P.r1) return;
+    const int nc = (P.cols + CH - 1) / CH;
+    const int i = r - P.r0;
+    c1 = nc;
+    if (P.tri == TRI_LOWER) c1 = (i / CH + 1 < nc) ? i / CH + 1 : nc;
+    if (P.tri == TRI_UPPER) c0 = (i / CH < nc) ? i / CH : nc;
+}
+
+__host__ __device__ inline int row_items(const Phase& ph, int CH, int r) {
+    int t = 0;
+    for (int q = 0; q < ph.np; ++q) {
+        int c0, c1;
+        part_chunks(ph.p[q], CH, r, c0, c1);
+        t += c1 - c0;
+    }
+    return t;
+}
 
 __device__ __forceinline__ unsigned long long gtimer() {
     unsigned long long t;
@@ -139,22 +191,24 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity) {
     return true;
 }
 
-// Ring of chunk slots in shared memory.  Slot s holds the chunks g with
-// g % S == s; its fill number is g / S.  full[s] completes one phase per copy
-// (producer arrival + transaction bytes), empty[s] one phase per consumption
-// (one arrival of the consuming warp).  A parity wait names the phase it waits
-// for exactly only while the waiter is at most one phase ahead, so every slot
-// has one owner on each side and each owner handles its slot's fills in order:
+// Ring of chunk slots in shared memory.  The block's chunks are numbered in one
+// sequence over phases and iterations; chunk g goes to slot g % S, its fill
+// number is g / S.  full[s] completes one phase per copy (producer arrival +
+// transaction bytes), empty[s] one phase per consumption (one arrival of the
+// consuming warp).  A parity wait names the phase it waits for exactly only
+// while the waiter is at most one phase ahead, so every slot has one owner on
+// each side and each owner handles its slot's fills in order:
 //  - producer lane s % 32 issues every fill of slot s; before fill f it waits
 //    for the consumption of fill f - 1, and it had waited for that of f - 2
 //    before issuing f - 1;
-//  - S is a multiple of the consumer warp count W and chunk g goes to consumer
-//    warp g % W, so slot s is always consumed by warp s % W,
-//    which has consumed fill f - 1 (hence seen it land) before it waits for f.
+//  - consumer warp s % W consumes every fill of slot s (W consumer warps), in
+//    order, so it has consumed fill f - 1 (hence seen it land) before it waits
+//    for fill f.
 // Neither side waits on anything but earlier chunks, so the ring cannot
 // deadlock.
 struct Ring {
     unsigned char* buf;
+    int slot_bytes;
     uint64_t* full;
     uint64_t* empty;
     int* last_fill;          // per slot: fill number of the last copy issued, or -1
@@ -166,11 +220,12 @@ struct Ring {
 template <int NT>
 __device__ __forceinline__ void csync() { asm volatile("bar.sync 1, %0;" ::"n"(Blk<NT>::threads) : "memory"); }
 
-// Grid barrier over the consumers: thread 0 of each block adds 1 to a monotonic
-// counter (release) and polls it (acquire) until every block of this round has
-// arrived; `target` advances by the block count per barrier.  A wait failure
-// anywhere (`*err` of this block, a timeout here) is published in b->err and
-// makes every block's barrier return false.  Bounded by kWaitNs.
+// Grid barrier over the consumers: thread 0 of each block adds 1 to the
+// monotonic counter (release; the block barrier before it orders the block's
+// writes) and spins on it (acquire) until every block of this round has
+// arrived; `target` advances by the block count per barrier.  A failure of
+// this block (*err) or a timeout here sets the error bit, which ends every
+// block's wait and makes every block's barrier return false.  Bounded by kWaitNs.
 template <int NT>
 __device__ __forceinline__ bool grid_sync(GridBar* b, unsigned nblocks, unsigned& target, const int* err,
                                           int* s_flag) {
@@ -179,101 +234,68 @@ __device__ __forceinline__ bool grid_sync(GridBar* b, unsigned nblocks, unsigned
     if (nblocks == 1) {   // a one-block grid: the block barrier above is the whole barrier
         if (threadIdx.x == 0) {
             const int e = *((volatile const int*)err);
-            if (e) atomicExch(&b->err, 2);
+            if (e) atomicOr(&b->count, kBarErr);
             *s_flag = e;
         }
         csync<NT>();
         return *s_flag == 0;
     }
     if (threadIdx.x == 0) {
-        if (*((volatile const int*)err)) atomicExch(&b->err, 2);
-        __threadfence();
+        if (*((volatile const int*)err)) atomicOr(&b->count, kBarErr);
         asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&b->count) : "memory");
-        if ((int)(ld_acquire(&b->count) - target) < 0) {
-            // poll with a short back-off: 152 blocks polling one word without it
-            // slow down the arrivals they wait for
+        unsigned v = ld_acquire(&b->count);
+        if (!(v & kBarErr) && (int)((v & ~kBarErr) - target) < 0) {
             const unsigned long long t0 = gtimer();
             unsigned polls = 0;
-            while ((int)(ld_acquire(&b->count) - target) < 0) {
-                __nanosleep(32);
-                if ((++polls & 15) == 0 && gtimer() - t0 > kWaitNs) {
-                    atomicExch(&b->err, 1);
+            while (true) {
+                v = ld_acquire(&b->count);
+                if ((v & kBarErr) || (int)((v & ~kBarErr) - target) >= 0) break;
+                if ((++polls & 1023) == 0 && gtimer() - t0 > kWaitNs) {
+                    atomicOr(&b->count, kBarErr);
+                    v = kBarErr;
                     break;
                 }
             }
         }
-        __threadfence();
-        *s_flag = *((volatile int*)&b->err);
+        *s_flag = (v & kBarErr) ? 1 : 0;
     }
     csync<NT>();
     return *s_flag == 0;
 }
 
-// Items of a chunked GEMV phase: (row, chunk) pairs, chunk-column-major, with
-// the chunks that lie entirely outside a triangle left out so that the work is
-// spread evenly.  Chunk column c holds rows [r0(c), r1(c)): all rows
-// (TRI_NONE), rows >= c*CH (lower), rows < (c+1)*CH (upper).
-template <int TRI>
-__device__ __forceinline__ void chunk_rows(int c, int CH, int rows, int& r0, int& r1) {
-    r0 = 0;
-    r1 = rows;
-    if (TRI == TRI_LOWER) r0 = min(rows, c * CH);
-    if (TRI == TRI_UPPER) r1 = min(rows, (c + 1) * CH);
-}
-
-template <int TRI>
-__device__ __forceinline__ int chunk_items(int rows, int cols, int CH) {
-    const int nc = (cols + CH - 1) / CH;
-    if (TRI == TRI_NONE) return rows * nc;
-    int t = 0;
-    for (int c = 0; c < nc; ++c) {
-        int r0, r1;
-        chunk_rows<TRI>(c, CH, rows, r0, r1);
-        t += r1 - r0;
+// Position in a block's item sequence of one phase: (row, part, chunk) and the
+// chunk's index k within its row; steps forward over rows in O(rows skipped).
+// CH: elements of one chunk.
+struct Walk {
+    int CH;
+    int row, p, c, c1, k;
+    __host__ __device__ __forceinline__ void first_of_row(const Phase& ph, int r) {
+        row = r;
+        k = 0;
+        p = -1;
+        next_part(ph);
     }
-    return t;
-}
-
-// This block's contiguous item range [b0, b0 + cnt) of a phase.
-template <int TRI>
-__device__ __forceinline__ void block_range(int rows, int cols, int CH, int& b0, int& cnt) {
-    const int nitems = chunk_items<TRI>(rows, cols, CH);
-    const int per = (nitems + (int)gridDim.x - 1) / (int)gridDim.x;
-    b0 = (int)blockIdx.x * per;
-    cnt = max(0, min(nitems, b0 + per) - b0);
-}
-
-// (row, chunk column) of an item, walked forward from a starting item by
-// non-negative steps: one division when it starts, additions after.
-template <int TRI>
-struct ItemWalk {
-    int rows, nc, CH;
-    int it = 0, c = 0, base = 0, r0 = 0, r1 = 0, row = 0;
-    __device__ __forceinline__ ItemWalk(int rows_, int nc_, int CH_, int first) : rows(rows_), nc(nc_), CH(CH_) {
-        if constexpr (TRI == TRI_NONE) {
-            it = first;
-            c = first / rows;
-            row = first - c * rows;
-        } else {
-            chunk_rows<TRI>(0, CH, rows, r0, r1);
-            step(first);
+    // the next (row, part) with chunks, from part p + 1 of `row` on
+    __host__ __device__ __forceinline__ void next_part(const Phase& ph) {
+        while (true) {
+            if (++p >= ph.np) {
+                if (++row >= ph.rows) { c = c1 = 0; return; }
+                p = -1;
+                k = 0;
+                continue;
+            }
+            int c0;
+            part_chunks(ph.p[p], CH, row, c0, c1);
+            if (c0 < c1) { c = c0; return; }
         }
     }
-    __device__ __forceinline__ void step(int d) {
-        it += d;
-        if constexpr (TRI == TRI_NONE) {
-            row += d;
-            while (row >= rows) {
-                row -= rows;
-                ++c;
-            }
-        } else {
-            while (it >= base + (r1 - r0) && c < nc - 1) {
-                base += r1 - r0;
-                ++c;
-                chunk_rows<TRI>(c, CH, rows, r0, r1);
-            }
-            row = r0 + (it - base);
+    __host__ __device__ __forceinline__ void step(const Phase& ph, int d) {
+        while (d > 0) {
+            const int rem = c1 - c - 1;   // items after the current one in this (row, part)
+            if (d <= rem) { c += d; k += d; return; }
+            d -= rem + 1;
+            k += rem + 1;
+            next_part(ph);
         }
     }
 };
@@ -290,31 +312,43 @@ struct RingPos {
     }
 };
 
-// Producer side of one phase: each lane copies the items whose slot it owns
+// Distance along the ring from slot `from` to slot `to` (0..S-1).
+__device__ __forceinline__ int ring_dist(int from, int to, int S) { return to >= from ? to - from : to + S - from; }
+
+// This block's rows [rb0, rb1) and item count of a phase (host-balanced table).
+struct BlockRange {
+    int rb0, rb1, cnt;
+};
+__device__ __forceinline__ BlockRange block_range(const int2* __restrict__ tbl, const Phase& ph) {
+    const int2 a = tbl[ph.tbl + blockIdx.x], b = tbl[ph.tbl + blockIdx.x + 1];
+    return BlockRange{a.x, b.x, b.y - a.y};
+}
+
+// Producer side of one phase: each lane copies the items whose slots it owns
 // (slots lane and lane + 32), in increasing order.  The lanes poll together (a
 // non-blocking test of their slot's empty barrier per round), so a lane whose
 // slot is still in use never holds up a lane whose slot is free.  `pos` is the
 // ring position of the phase's first item (advanced past the phase).  Returns
 // false (in every lane) once the consumers have stopped or the phase took
 // longer than kWaitNs.
-template <typename TM, int TRI>
-__device__ __forceinline__ bool produce_phase(const TM* __restrict__ M, int rows, int cols, long long ld,
-                                              const Ring& R, RingPos& pos) {
-    constexpr int CH = Chunk<TM>::n;
+template <typename TM>
+__device__ __forceinline__ bool produce_phase(const Phase& ph, const BlockRange br, const Ring& R, RingPos& pos) {
+    const int CH = R.slot_bytes / (int)sizeof(TM);
     const int lane = threadIdx.x & 31;
-    const int nc = (cols + CH - 1) / CH;
     const int S = R.S;
-    int b0, cnt;
-    block_range<TRI>(rows, cols, CH, b0, cnt);
-    // owned slots, and the distance from one slot to another along the ring
+    const int cnt = br.cnt;
     const int o1 = lane < S ? lane : -1, o2 = lane + 32 < S ? lane + 32 : -1;
-    auto dist = [&](int from, int to) { return to >= from ? to - from : to + S - from; };
     int i = cnt;
-    if (o1 >= 0) i = dist(pos.slot, o1);
-    if (o2 >= 0) i = min(i, dist(pos.slot, o2));
+    if (o1 >= 0) i = ring_dist(pos.slot, o1, S);
+    if (o2 >= 0) i = min(i, ring_dist(pos.slot, o2, S));
     RingPos me = pos;
-    me.advance(i < cnt ? i : 0, S);
-    ItemWalk<TRI> w(rows, nc, CH, b0 + (i < cnt ? i : 0));
+    Walk w;
+    w.CH = CH;
+    if (i < cnt) {
+        me.advance(i, S);
+        w.first_of_row(ph, br.rb0);
+        w.step(ph, i);
+    }
     bool ok = true;
     unsigned polls = 0;
     const unsigned long long t0 = gtimer();
@@ -325,18 +359,20 @@ __device__ __forceinline__ bool produce_phase(const TM* __restrict__ M, int rows
             const int slot = me.slot, fill = me.fill;
             // the slot is free once its previous chunk has been consumed
             if (fill == 0 || mbar_test(&R.empty[slot], (unsigned)((fill - 1) & 1))) {
+                const Part& P = ph.p[w.p];
                 const long long e0 = (long long)w.c * CH;
-                const unsigned bytes = (unsigned)(min((long long)CH, ld - e0) * (long long)sizeof(TM));
+                const unsigned bytes = (unsigned)(min((long long)CH, P.ld - e0) * (long long)sizeof(TM));
+                const TM* src = static_cast<const TM*>(P.M) + (long long)(w.row - P.r0) * P.ld + e0;
                 R.last_fill[slot] = fill;
                 mbar_expect_tx(&R.full[slot], bytes);
-                bulk_g2s(R.buf + (size_t)slot * kSlotBytes, M + (long long)w.row * ld + e0, bytes, &R.full[slot]);
+                bulk_g2s(R.buf + (size_t)slot * R.slot_bytes, src, bytes, &R.full[slot]);
                 // next owned slot: the lane's other slot, else the same slot one lap later
                 const int other = (slot == o1) ? o2 : o1;
-                const int d = (other >= 0) ? dist(slot, other) : S;
+                const int d = (other >= 0) ? ring_dist(slot, other, S) : S;
                 i += d;
                 if (i < cnt) {
                     me.advance(d, S);
-                    w.step(d);
+                    w.step(ph, d);
                 }
             }
         }
@@ -346,134 +382,98 @@ __device__ __forceinline__ bool produce_phase(const TM* __restrict__ M, int rows
     return __all_sync(0xffffffffu, ok);
 }
 
-// Consumer side of one phase: part[c * pld + row] = chunk c of row `row` of M . xs
-// (chunk-major, so that the next phase's per-row sums load coalesced).  Warp w
-// takes the items whose slot is w modulo the consumer warp count (S is a
-// multiple of it).
-template <typename TM, int TRI, int NT>
-__device__ __forceinline__ void gemv_ring(const Ring& R, RingPos& pos, int rows, int cols, long long ld,
-                                          const TM* __restrict__ xs, TM* __restrict__ part, int pld,
-                                          int* err) {
+// Consumer side of one phase: spart[lrow * ncmax + k] = chunk k of local row
+// lrow dotted with the staged vector xs.  Warp w takes the items of the slots
+// w, w + W, w + 2W, ... (below S).
+template <typename TM, int NT>
+__device__ __forceinline__ void consume_phase(const Phase& ph, const BlockRange br, const Ring& R, RingPos& pos,
+                                              const TM* __restrict__ xs, TM* __restrict__ spart, int* err) {
     using VT = Vec16<TM>;
     using V = typename VT::type;
-    constexpr int CH = Chunk<TM>::n;
     constexpr int VN = VT::n;
+    constexpr int W = Blk<NT>::warps;
+    const int CH = R.slot_bytes / (int)sizeof(TM);
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    const int nc = (cols + CH - 1) / CH;
     const int S = R.S;
-    int b0, cnt;
-    block_range<TRI>(rows, cols, CH, b0, cnt);
-    const V* xv = reinterpret_cast<const V*>(xs);
-    constexpr int W = Blk<NT>::warps;
-    const int first = (warp - pos.slot % W + W) % W;
-    if (first < cnt) {
+    const int cnt = br.cnt;
+    // owned slots: warp, warp + W, ... (below S); the one after slot s is s + W, or
+    // `warp` on the next lap.  The first owned item is the nearest owned slot.
+    int i = cnt;
+    for (int s = warp; s < S; s += W) i = min(i, ring_dist(pos.slot, s, S));
+    if (i < cnt) {
         RingPos me = pos;
-        me.advance(first, S);
-        ItemWalk<TRI> w(rows, nc, CH, b0 + first);
-        for (int i = first; i < cnt; i += W) {
-            const int vbase = w.c * (CH / VN);
+        me.advance(i, S);
+        Walk w;
+        w.CH = CH;
+        w.first_of_row(ph, br.rb0);
+        w.step(ph, i);
+        while (true) {
+            const Part& P = ph.p[w.p];
             const int slot = me.slot;
             if (!mbar_wait(&R.full[slot], (unsigned)(me.fill & 1))) *err = 1;
-            const V* sv = reinterpret_cast<const V*>(R.buf + (size_t)slot * kSlotBytes);
-            const int vend = (int)(ld / VN) - vbase;   // vectors of this row from the chunk start
-            TM acc = TM(0);
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const int v = lane + 32 * k;
-                const V m = (v < vend) ? sv[v] : V{};
-                acc = VT::dot(m, xv[vbase + v], acc);
+            const V* sv = reinterpret_cast<const V*>(R.buf + (size_t)slot * R.slot_bytes);
+            const V* xv = reinterpret_cast<const V*>(xs + P.xoff + w.c * CH);
+            // vectors copied into the slot (the row's padding columns are zeros)
+            const int vend = (int)(min((long long)CH, P.ld - (long long)w.c * CH) / VN);
+            TM a0 = TM(0), a1 = TM(0);
+            int v = lane;
+#pragma unroll 2
+            for (; v + 32 < vend; v += 64) {
+                a0 = VT::dot(sv[v], xv[v], a0);
+                a1 = VT::dot(sv[v + 32], xv[v + 32], a1);
             }
+            if (v < vend) a0 = VT::dot(sv[v], xv[v], a0);
             __syncwarp();
             if (lane == 0) mbar_arrive(&R.empty[slot]);
-            acc = warp_sum(acc);
-            if (lane == 0) part[(long long)w.c * pld + w.row] = acc;
-            if (i + W < cnt) {
-                me.advance(W, S);
-                w.step(W);
-            }
+            TM acc = warp_sum(a0 + a1);
+            if (lane == 0) spart[(w.row - br.rb0) * ph.ncmax + w.k] = acc;
+            const int d = (slot + W < S) ? W : warp + S - slot;
+            if (i + d >= cnt) break;
+            i += d;
+            me.advance(d, S);
+            w.step(ph, d);
         }
     }
     pos.advance(cnt, S);
 }
 
-// Chunk sums of four rows j[0..3] at once (rows >= len give 0): for each row the
-// chunks are added in increasing order, the loads of all four rows and four
-// consecutive chunks issued together.
-template <typename TM, int TRI, typename AT>
-__device__ __forceinline__ void sum_chunks4(const TM* __restrict__ part, int pld, int cols, const int* j,
-                                            int len, AT* out) {
-    constexpr int CH = Chunk<TM>::n;
-    const int nc = (cols + CH - 1) / CH;
-    int c0[4], c1[4];
-    int cmin = nc, cmax = 0;
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        c0[u] = 0;
-        c1[u] = (j[u] < len) ? nc : 0;
-        if (TRI == TRI_LOWER && j[u] < len) c1[u] = j[u] / CH + 1;
-        if (TRI == TRI_UPPER && j[u] < len) c0[u] = j[u] / CH;
-        out[u] = AT(0);
-        if (c0[u] < c1[u]) {
-            cmin = min(cmin, c0[u]);
-            cmax = max(cmax, c1[u]);
-        }
-    }
-    for (int c = cmin; c < cmax; c += 4) {
-        TM v[4][4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int cc = c + k;
-                v[u][k] = (cc >= c0[u] && cc < c1[u]) ? __ldcg(part + (long long)cc * pld + j[u]) : TM(0);
-            }
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int k = 0; k < 4; ++k) out[u] += (AT)v[u][k];
+// Sum each owned row's chunk partials in chunk order and write it to out[row].
+template <typename TM, int NT>
+__device__ __forceinline__ void row_sums(const Phase& ph, const BlockRange br, const TM* __restrict__ spart,
+                                         TM* __restrict__ out, int slot_bytes) {
+    const int CH = slot_bytes / (int)sizeof(TM);
+    for (int r = br.rb0 + (int)threadIdx.x; r < br.rb1; r += Blk<NT>::threads) {
+        const int nk = row_items(ph, CH, r);
+        const TM* sp = spart + (r - br.rb0) * ph.ncmax;
+        TM s = TM(0);
+        for (int k = 0; k < nk; ++k) s += sp[k];
+        out[r] = s;
     }
 }
 
-// Stage xs[j] for j < pad (zero from len on): rows are taken four per thread;
-// f(j, sum) turns a row's chunk sum into the staged value.
-template <int NT, typename TX, typename TM, int TRI, class F>
-__device__ __forceinline__ void stage_sum(TX* xs, const TM* part, int pld, int cols, int len, int pad, F f) {
-    using AT = typename Acc<TM>::type;
+// Stage a phase's input from the previous phase's output (see Phase).  Loads are
+// issued four per thread before any is used.
+template <int NT, typename TX>
+__device__ __forceinline__ void stage_input(const Phase& ph, TX* __restrict__ xs, const TX* __restrict__ out) {
     constexpr int T = Blk<NT>::threads;
-    for (int j0 = threadIdx.x; j0 < pad; j0 += 4 * T) {
-        int j[4];
-        AT sm[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) j[u] = j0 + u * T;
-        sum_chunks4<TM, TRI, AT>(part, pld, cols, j, len, sm);
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-            if (j[u] < pad) xs[j[u]] = (j[u] < len) ? f(j[u], sm[u]) : TX(0);
-    }
-}
-
-// stage_sum with an operand loaded before the partials: pre(j) is issued for the
-// four rows together with their partial loads, and f(j, sum, pre(j)) makes the
-// staged value, so a loop-invariant vector costs no extra round trip.
-template <int NT, typename TX, typename TM, int TRI, class P, class F>
-__device__ __forceinline__ void stage_sum_pre(TX* xs, const TM* part, int pld, int cols, int len, int pad, P pre,
-                                              F f) {
-    using AT = typename Acc<TM>::type;
-    constexpr int T = Blk<NT>::threads;
-    for (int j0 = threadIdx.x; j0 < pad; j0 += 4 * T) {
-        int j[4];
-        AT sm[4];
-        decltype(pre(0)) pv[4];
+    for (int j0 = threadIdx.x; j0 < ph.in_pad; j0 += 4 * T) {
+        TX v[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            j[u] = j0 + u * T;
-            pv[u] = (j[u] < len) ? pre(j[u]) : decltype(pre(0))(0);
+            const int j = j0 + u * T;
+            v[u] = TX(0);
+            if (j < ph.in_len1) {
+                v[u] = __ldcg(out + j);
+            } else if (ph.in_len2 > 0 && j >= ph.in_off2 && j < ph.in_off2 + ph.in_len2) {
+                v[u] = (TX)ph.in_s2 * __ldcg(out + ph.in_len1 + (j - ph.in_off2));
+            }
         }
-        sum_chunks4<TM, TRI, AT>(part, pld, cols, j, len, sm);
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-            if (j[u] < pad) xs[j[u]] = (j[u] < len) ? f(j[u], sm[u], pv[u]) : TX(0);
+        for (int u = 0; u < 4; ++u) {
+            const int j = j0 + u * T;
+            if (j < ph.in_pad) xs[j] = v[u];
+        }
     }
 }
 
@@ -495,72 +495,80 @@ __device__ __forceinline__ AT block_allsum(AT v, AT* sh) {
     return v;
 }
 
+// Two fixed-order sums at once.
+template <int NT, typename AT>
+__device__ __forceinline__ void block_allsum2(AT& a, AT& b, AT* sh) {
+    a = warp_sum(a);
+    b = warp_sum(b);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) { sh[w] = a; sh[16 + w] = b; }
+    csync<NT>();
+    if (threadIdx.x < 32) {
+        AT ra = (l < Blk<NT>::warps) ? sh[l] : AT(0);
+        AT rb = (l < Blk<NT>::warps) ? sh[16 + l] : AT(0);
+        ra = warp_sum(ra);
+        rb = warp_sum(rb);
+        if (l == 0) { sh[32] = ra; sh[33] = rb; }
+    }
+    csync<NT>();
+    a = sh[32];
+    b = sh[33];
+    csync<NT>();
+}
+
 template <typename TO, typename TP>
 struct FusedArgs {
     int n, m1, m2;
-    // operator (precision TO)
-    const TO *CWT, *WH, *Et, *EtT, *WHT, *CW;
-    long long ldCWT, ldWH, ldEt, ldEtT, ldWHT, ldCW;
-    // pcg_form 1: B = L^{-1}[C'; 0] ((n+m1) x m2) and B', partials of B p
-    int wform;
-    const TO *BW, *BWT;
-    long long ldBW, ldBWT;
-    TO* PW;
-    int ldPW;
-    // preconditioner (precision TP)
-    const TP *WPl, *WPu;
-    long long ldWP;
-    const TP* sg;
-    // vectors
+    Phase ph[kMaxPhases];   // operator phases 0..nop-1, then the P_H phases nop..nop+npc-1
+    int nop, npc;           // npc: 1 (the symmetric inverse P~^{-1}) or 2 (its two triangular factors)
+    const int2* tbl;        // (first row, first item) of every block, per phase
+    TO* out[kMaxPhases];    // output vectors of the operator phases
+    TP* outP[2];            // outputs of the P_H phases
+    const TP* sg;           // Jacobi scaling of P_H
     const TO* D;
     const TO* Dinv;
     TO* x;
-    TO *r0, *r1, *p0, *p1;
-    // chunk partials
-    TO *PU, *PZ1, *PZ2, *PT, *PY, *PQ;
-    TP *PV, *PZ;
-    int ldU, ldZ1, ldZ2, ldT, ldY, ldQ, ldV, ldZ;
+    const TO* r_in;         // entry residual (= rhs) and search direction (= z0)
+    const TO* p_in;
     PcgState* st;      // entry: rz_cur, tol2, maxit, done (from pcg_init); exit: iter, rr, done
     GridBar* bar;      // zeroed before the launch
     size_t xs_bytes;   // bytes of the staged-vector region of shared memory (16-byte multiple)
+    size_t spart_off;  // byte offset of the per-row chunk partials
     size_t ring_off;   // byte offset of the slot ring (128-byte aligned)
     int slots;         // ring depth S
-    unsigned long long* tstamp;   // optional: %globaltimer at phase marks of the first 4 iterations
+    int slot_bytes;    // bytes of one slot (a multiple of 16)
+    unsigned long long* tstamp;   // optional: %globaltimer marks of block 0 (4 iterations x 32) and
+                                  // every block's phase ends of iteration 2 (8 x grid, after 128)
     int leave_early;              // failure-detection test: block 0 leaves before its first grid barrier
 };
 
 // Shared-memory layout of the persistent kernel: staged vector, three m2-vector
-// caches, then the ring (slots, full and empty mbarriers, last-fill words, stop flag).
+// caches (q or z, r, p in TO), the per-row chunk partials, then the ring (slots,
+// full and empty mbarriers, last-fill words, stop flag).
 template <typename TO>
-inline size_t fused_ring_offset(size_t xs_bytes, int m2) {
+inline size_t fused_spart_offset(size_t xs_bytes, int m2) {
     const size_t o = xs_bytes + 3 * (size_t)m2 * sizeof(TO);
+    return (o + 15) / 16 * 16;
+}
+inline size_t fused_ring_offset(size_t spart_off, size_t spart_bytes) {
+    const size_t o = spart_off + spart_bytes;
     return (o + 127) / 128 * 128;
 }
-inline size_t fused_smem_bytes(size_t ring_off, int slots) {
-    return ring_off + (size_t)slots * (kSlotBytes + 2 * sizeof(uint64_t) + sizeof(int)) + 16;
+inline size_t fused_smem_bytes(size_t ring_off, int slots, int slot_bytes) {
+    return ring_off + (size_t)slots * (slot_bytes + 2 * sizeof(uint64_t) + sizeof(int)) + 16;
 }
 
 // The producer's sequence of phases, the consumers' loop below in the same order.
 template <typename TO, typename TP, int PC>
-__device__ void pcg_producer(const FusedArgs<TO, TP>& a, const Ring& R) {
-    const int n = a.n, m1 = a.m1, m2 = a.m2;
+__device__ void pcg_producer(const FusedArgs<TO, TP>& a, const BlockRange* brs, const Ring& R) {
     RingPos g;
     while (!*R.stop) {   // (a block may own no chunk of any phase: it polls the stop flag here)
-        if (a.wform) {
-            if (!produce_phase<TO, TRI_NONE>(a.BW, n + m1, m2, a.ldBW, R, g)) break;
-            if (!produce_phase<TO, TRI_NONE>(a.BWT, m2, n + m1, a.ldBWT, R, g)) break;
-        } else {
-            if (!produce_phase<TO, TRI_NONE>(a.CWT, n, m2, a.ldCWT, R, g)) break;
-            if (!produce_phase<TO, TRI_LOWER>(a.WH, n, n, a.ldWH, R, g)) break;
-            if (m1 > 0 && !produce_phase<TO, TRI_NONE>(a.Et, m1, n, a.ldEt, R, g)) break;
-            if (!produce_phase<TO, TRI_UPPER>(a.WHT, n, n, a.ldWHT, R, g)) break;
-            if (m1 > 0 && !produce_phase<TO, TRI_NONE>(a.EtT, n, m1, a.ldEtT, R, g)) break;
-            if (!produce_phase<TO, TRI_NONE>(a.CW, m2, n, a.ldCW, R, g)) break;
-        }
-        if (PC == PC_H_K) {
-            if (!produce_phase<TP, TRI_LOWER>(a.WPl, m2, m2, a.ldWP, R, g)) break;
-            if (!produce_phase<TP, TRI_UPPER>(a.WPu, m2, m2, a.ldWP, R, g)) break;
-        }
+        bool ok = true;
+        for (int k = 0; k < a.nop && ok; ++k) ok = produce_phase<TO>(a.ph[k], brs[k], R, g);
+        if (!ok) break;
+        if (PC == PC_H_K)
+            for (int k = a.nop; k < a.nop + a.npc && ok; ++k) ok = produce_phase<TP>(a.ph[k], brs[k], R, g);
+        if (!ok) break;
     }
     // drain: every copy issued lands before the block's shared memory goes away
     __syncwarp();
@@ -571,14 +579,13 @@ __device__ void pcg_producer(const FusedArgs<TO, TP>& a, const Ring& R) {
     }
 }
 
-// kind: PC_L_K (z = r / D), PC_H_K (z = Sg W' W Sg r), PC_NONE_K (z = r).
-// Entry state (from pcg_init): x = 0, r = r0 = rhs, p = p0 = z0, st->rz_cur = r'z,
-// st->tol2 = tol^2 |rhs|^2, st->maxit.  Shared memory: the staged vector
-// (xs_bytes), three m2-vectors in TO (q = K_F p, r and p of the current
-// iteration), then the ring.
+// kind: PC_L_K (z = r / D), PC_H_K (z = Sg P~^{-1} Sg r), PC_NONE_K (z = r).
+// Entry state (from pcg_init): x = 0, r = rhs, p = z0, st->rz_cur = r'z,
+// st->tol2 = tol^2 |rhs|^2, st->maxit.
 template <typename TO, typename TP, int PC, int NT>
-__global__ void __launch_bounds__(NT, NT == kSmallBlock ? 2 : 1) pcg_fused_kernel(const FusedArgs<TO, TP> a) {
-    constexpr int kFusedThreads = Blk<NT>::threads;
+__global__ void __launch_bounds__(NT, NT == kSmallBlock ? 2 : 1)
+    pcg_fused_kernel(const __grid_constant__ FusedArgs<TO, TP> a) {
+    constexpr int T = Blk<NT>::threads;
     PCG_COUNT_KERNEL();
     extern __shared__ __align__(128) unsigned char pcg_smem[];
     TO* xs = reinterpret_cast<TO*>(pcg_smem);
@@ -588,18 +595,22 @@ __global__ void __launch_bounds__(NT, NT == kSmallBlock ? 2 : 1) pcg_fused_kerne
     TO* pcs = rc + a.m2;
     Ring R;
     R.S = a.slots;
+    R.slot_bytes = a.slot_bytes;
     R.buf = pcg_smem + a.ring_off;
-    R.full = reinterpret_cast<uint64_t*>(R.buf + (size_t)R.S * kSlotBytes);
+    R.full = reinterpret_cast<uint64_t*>(R.buf + (size_t)R.S * a.slot_bytes);
     R.empty = R.full + R.S;
     R.last_fill = reinterpret_cast<int*>(R.empty + R.S);
     R.stop = reinterpret_cast<volatile int*>(R.last_fill + R.S);
     using AT = typename Acc<TO>::type;
+    using ATP = typename Acc<TP>::type;
     __shared__ AT sh[40];
     __shared__ int s_flag;
     __shared__ int s_err;
-    const int n = a.n, m1 = a.m1, m2 = a.m2;
+    __shared__ BlockRange s_br[kMaxPhases];
+    const int m2 = a.m2;
     const int tid = threadIdx.x;
     const unsigned nblocks = gridDim.x;
+    const int nph = a.nop + (PC == PC_H_K ? a.npc : 0);
 
     if (__ldcg(&a.st->done)) return;
     if (tid == 0) {
@@ -613,25 +624,29 @@ __global__ void __launch_bounds__(NT, NT == kSmallBlock ? 2 : 1) pcg_fused_kerne
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
+    if (tid < nph) s_br[tid] = block_range(a.tbl, a.ph[tid]);
     __syncthreads();
-    if (tid >= kFusedThreads) {
-        pcg_producer<TO, TP, PC>(a, R);
+    if (tid >= T) {
+        pcg_producer<TO, TP, PC>(a, s_br, R);
         return;
     }
 
     // ------------------------------------------------------------ consumers
+    TO* spart = reinterpret_cast<TO*>(pcg_smem + a.spart_off);
+    TP* spartP = reinterpret_cast<TP*>(pcg_smem + a.spart_off);
     // slice of the m2-vectors this block owns for writes
     const int per = (m2 + nblocks - 1) / nblocks;
     const int own0 = blockIdx.x * per, own1 = min(m2, own0 + per);
-    constexpr int CHO = Chunk<TO>::n, CHP = Chunk<TP>::n;
-    const int padO_n = ((n + CHO - 1) / CHO) * CHO, padO_m2 = ((m2 + CHO - 1) / CHO) * CHO;
-    const int padO_m1 = ((m1 + CHO - 1) / CHO) * CHO, padP_m2 = ((m2 + CHP - 1) / CHP) * CHP;
-    TO* xs2 = xs + padO_n;   // z2, beside z1, for the back solve
-    const int padO_nm1 = ((n + m1 + CHO - 1) / CHO) * CHO;
-    const int qcols = a.wform ? n + m1 : n;   // columns of the matrix whose partials make C y
+    // staged m2-vectors are padded to 32 elements (the leading dimension of C' and P~^{-1})
+    const int padO_m2 = ((m2 + 31) / 32) * 32, padP_m2 = padO_m2;
     const bool stamp = a.tstamp != nullptr && blockIdx.x == 0 && tid == 0;
     auto mark = [&](int it, int ph) {
         if (stamp && it < 4) a.tstamp[it * 32 + ph] = gtimer();
+    };
+    // every block's phase end (before its barrier arrival) in iteration 2
+    auto mark_all = [&](int it, int ph) {
+        if (a.tstamp != nullptr && tid == 0 && it == 2 && ph < 8)
+            a.tstamp[128 + ph * nblocks + blockIdx.x] = gtimer();
     };
     unsigned target = 0;
     RingPos g;   // ring position of the next chunk
@@ -639,7 +654,7 @@ __global__ void __launch_bounds__(NT, NT == kSmallBlock ? 2 : 1) pcg_fused_kerne
     auto leave = [&]() {
         csync<NT>();
         if (tid == 0) {
-            if (s_err) atomicExch(&a.bar->err, 2);
+            if (s_err) atomicOr(&a.bar->count, kBarErr);
             *R.stop = 1;
         }
     };
@@ -651,16 +666,14 @@ __global__ void __launch_bounds__(NT, NT == kSmallBlock ? 2 : 1) pcg_fused_kerne
     int it = 0;
     int done = 0;
     AT rr = AT(0);
-    TO* pc = a.p0;  TO* pn = a.p1;
-    TO* rcur = a.r0; TO* rnext = a.r1;
 
     // first iteration: p and r from the entry state; xs = p
-    for (int j = tid; j < m2; j += kFusedThreads) {
-        pcs[j] = __ldcg(pc + j);
-        rc[j] = __ldcg(rcur + j);
+    for (int j = tid; j < m2; j += T) {
+        pcs[j] = __ldcg(a.p_in + j);
+        rc[j] = __ldcg(a.r_in + j);
     }
     csync<NT>();
-    for (int j = tid; j < padO_m2; j += kFusedThreads) xs[j] = (j < m2) ? pcs[j] : TO(0);
+    for (int j = tid; j < padO_m2; j += T) xs[j] = (j < m2) ? pcs[j] : TO(0);
     csync<NT>();
 
     // failure-detection test: block 0 stops before the first grid barrier, as a block
@@ -669,81 +682,56 @@ __global__ void __launch_bounds__(NT, NT == kSmallBlock ? 2 : 1) pcg_fused_kerne
 
     while (true) {
         mark(it, 0);
-        if (a.wform) {
-            // ---- W1 (a6-a7): w = B p, B = L^{-1}[C'; 0] (rows R^{-T} C', then Et C')
-            gemv_ring<TO, TRI_NONE, NT>(R, g, n + m1, m2, a.ldBW, xs, a.PW, a.ldPW, &s_err);
-            mark(it, 11);
-            if (!gsync()) { leave(); return; }
-            mark(it, 1);
-            // ---- W2 (a7-a8): C y = B' J w with J = diag(I_n, -I_m1)
-            stage_sum<NT, TO, TO, TRI_NONE>(xs, a.PW, a.ldPW, m2, n + m1, padO_nm1,
-                                            [&](int j, AT v) { return (TO)(j < n ? v : -v); });
-            csync<NT>();
-            mark(it, 16);
-            gemv_ring<TO, TRI_NONE, NT>(R, g, m2, n + m1, a.ldBWT, xs, a.PQ, a.ldQ, &s_err);
-            mark(it, 17);
-            if (!gsync()) { leave(); return; }
-            mark(it, 6);
-        } else {
-            // ---- P1 (a6): u = C' p
-            gemv_ring<TO, TRI_NONE, NT>(R, g, n, m2, a.ldCWT, xs, a.PU, a.ldU, &s_err);
-            mark(it, 11);
-            if (!gsync()) { leave(); return; }
-            mark(it, 1);
-            // ---- P2 (a7, forward solve with L): z1 = R^{-T} u, Et u (z2 = -Et u)
-            stage_sum<NT, TO, TO, TRI_NONE>(xs, a.PU, a.ldU, m2, n, padO_n, [&](int, AT v) { return (TO)v; });
-            csync<NT>();
-            mark(it, 12);
-            gemv_ring<TO, TRI_LOWER, NT>(R, g, n, n, a.ldWH, xs, a.PZ1, a.ldZ1, &s_err);
-            if (m1 > 0) gemv_ring<TO, TRI_NONE, NT>(R, g, m1, n, a.ldEt, xs, a.PZ2, a.ldZ2, &s_err);
-            mark(it, 13);
-            if (!gsync()) { leave(); return; }
-            mark(it, 2);
-            // ---- P3 (a7, back solve with L'): y = R^{-1} z1 + Et' z2
-            stage_sum<NT, TO, TO, TRI_LOWER>(xs, a.PZ1, a.ldZ1, n, n, padO_n, [&](int, AT v) { return (TO)v; });
-            if (m1 > 0)
-                stage_sum<NT, TO, TO, TRI_NONE>(xs2, a.PZ2, a.ldZ2, n, m1, padO_m1, [&](int, AT v) { return (TO)(-v); });
-            csync<NT>();
-            mark(it, 14);
-            gemv_ring<TO, TRI_UPPER, NT>(R, g, n, n, a.ldWHT, xs, a.PY, a.ldY, &s_err);
-            if (m1 > 0) gemv_ring<TO, TRI_NONE, NT>(R, g, n, m1, a.ldEtT, xs2, a.PT, a.ldT, &s_err);
-            mark(it, 15);
-            if (!gsync()) { leave(); return; }
-            mark(it, 5);
-            // ---- P4 (a8): q = D p + C y
-            if (m1 > 0) {
-                stage_sum<NT, TO, TO, TRI_NONE>(xs, a.PT, a.ldT, m1, n, padO_n, [&](int, AT v) { return (TO)v; });
+        // ---- operator phases (a6-a8): K_F p = D p + C y, y from C'p and the K0 solve
+        for (int k = 0; k < a.nop; ++k) {
+            const Phase& ph = a.ph[k];
+            if (k > 0) {
+                stage_input<NT, TO>(ph, xs, a.out[k - 1]);
                 csync<NT>();
-                stage_sum<NT, TO, TO, TRI_UPPER>(xs, a.PY, a.ldY, n, n, padO_n,
-                                             [&](int j, AT v) { return (TO)(v + (AT)xs[j]); });
-            } else {
-                stage_sum<NT, TO, TO, TRI_UPPER>(xs, a.PY, a.ldY, n, n, padO_n, [&](int, AT v) { return (TO)v; });
+                mark(it, 10 + k);
             }
+            consume_phase<TO, NT>(ph, s_br[k], R, g, xs, spart, &s_err);
             csync<NT>();
-            mark(it, 16);
-            gemv_ring<TO, TRI_NONE, NT>(R, g, m2, n, a.ldCW, xs, a.PQ, a.ldQ, &s_err);
-            mark(it, 17);
+            row_sums<TO, NT>(ph, s_br[k], spart, a.out[k], a.slot_bytes);
+            mark(it, 15 + k);
+            mark_all(it, k);
             if (!gsync()) { leave(); return; }
-            mark(it, 6);
+            mark(it, 1 + k);
         }
 
-        // ---- P5 (a10): q = D p + C y (cached), alpha = r'z / p'q, x += alpha p, r -= alpha q
+        // ---- (a10) q = D p + w (cached), alpha = r'z / p'q, x += alpha p, r -= alpha q
         // (p'q is summed while q is staged: each thread takes its rows in increasing order)
         AT pq = AT(0);
-        stage_sum_pre<NT, TO, TO, TRI_NONE>(qc, a.PQ, a.ldQ, qcols, m2, m2, [&](int j) { return __ldg(a.D + j); },
-                                        [&](int j, AT v, TO dj) {
-                                            const TO q = (TO)fma((AT)dj, (AT)pcs[j], v);
-                                            pq = fma((AT)pcs[j], (AT)q, pq);
-                                            return q;
-                                        });
+        {
+            const TO* w = a.out[a.nop - 1];
+            for (int j0 = tid; j0 < m2; j0 += 4 * T) {
+                TO wv[4], dv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int j = j0 + u * T;
+                    wv[u] = j < m2 ? __ldcg(w + j) : TO(0);
+                    dv[u] = j < m2 ? __ldg(a.D + j) : TO(0);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int j = j0 + u * T;
+                    if (j < m2) {
+                        const TO q = (TO)fma((AT)dv[u], (AT)pcs[j], (AT)wv[u]);
+                        qc[j] = q;
+                        pq = fma((AT)pcs[j], (AT)q, pq);
+                    }
+                }
+            }
+        }
         pq = block_allsum<NT>(pq, sh);
+        mark(it, 6);
         // breakdown (p'q <= 0 or not finite): stop with the last iterate untouched
         if (!(pq > AT(0)) || !isfinite(pq)) { done = 3; break; }
         const AT alpha = rz / pq;
         const TO al = (TO)alpha;
         AT rrp = AT(0), rzp = AT(0);
 #pragma unroll 4
-        for (int j = tid; j < padO_m2; j += kFusedThreads) {
+        for (int j = tid; j < padO_m2; j += T) {
             if (j >= m2) {
                 if (PC == PC_H_K) { if (j < padP_m2) xp[j] = TP(0); } else xs[j] = TO(0);
                 continue;
@@ -751,10 +739,7 @@ __global__ void __launch_bounds__(NT, NT == kSmallBlock ? 2 : 1) pcg_fused_kerne
             const TO rn = fma(-al, qc[j], rc[j]);
             rc[j] = rn;
             rrp = fma((AT)rn, (AT)rn, rrp);
-            if (j >= own0 && j < own1) {
-                a.x[j] = fma(al, pcs[j], a.x[j]);
-                rnext[j] = rn;
-            }
+            if (j >= own0 && j < own1) a.x[j] = fma(al, pcs[j], a.x[j]);
             if (PC == PC_H_K) {
                 xp[j] = (TP)((AT)rn * (AT)__ldg(a.sg + j));
             } else {
@@ -763,49 +748,68 @@ __global__ void __launch_bounds__(NT, NT == kSmallBlock ? 2 : 1) pcg_fused_kerne
             }
         }
         if (PC == PC_H_K)
-            for (int j = padO_m2 + tid; j < padP_m2; j += kFusedThreads) xp[j] = TP(0);
-        rr = block_allsum<NT>(rrp, sh);
+            for (int j = padO_m2 + tid; j < padP_m2; j += T) xp[j] = TP(0);
+        if (PC == PC_H_K) {
+            rr = block_allsum<NT>(rrp, sh);
+        } else {
+            block_allsum2<NT>(rrp, rzp, sh);
+            rr = rrp;
+        }
         ++it;
+        mark(it - 1, 7);
         const bool finite = isfinite(rr) && isfinite(pq);
         if (!finite) { done = 3; break; }
         if ((double)rr <= tol2) { done = 1; break; }
         if (it >= maxit) { done = 2; break; }
-        mark(it - 1, 7);
 
         AT rz_new;
         if (PC == PC_H_K) {
-            csync<NT>();
-            // ---- P6 (a9): v = W rs, z = Sg W' v
-            gemv_ring<TP, TRI_LOWER, NT>(R, g, m2, m2, a.ldWP, xp, a.PV, a.ldV, &s_err);
-            mark(it - 1, 18);
-            if (!gsync()) { leave(); return; }
+            // ---- (a9) v = P~^{-1} (Sg r) (one symmetric phase, or W then W'), z = Sg v
+            for (int k = 0; k < a.npc; ++k) {
+                const Phase& ph = a.ph[a.nop + k];
+                if (k > 0) {
+                    stage_input<NT, TP>(ph, xp, a.outP[k - 1]);
+                    csync<NT>();
+                }
+                consume_phase<TP, NT>(ph, s_br[a.nop + k], R, g, xp, spartP, &s_err);
+                csync<NT>();
+                row_sums<TP, NT>(ph, s_br[a.nop + k], spartP, a.outP[k], a.slot_bytes);
+                mark(it - 1, 19 + k);
+                mark_all(it - 1, a.nop + k);
+                if (!gsync()) { leave(); return; }
+            }
             mark(it - 1, 8);
-            stage_sum<NT, TP, TP, TRI_LOWER>(xp, a.PV, a.ldV, m2, m2, padP_m2, [&](int, typename Acc<TP>::type v) { return (TP)v; });
-            csync<NT>();
-            mark(it - 1, 19);
-            gemv_ring<TP, TRI_UPPER, NT>(R, g, m2, m2, a.ldWP, xp, a.PZ, a.ldZ, &s_err);
-            mark(it - 1, 20);
-            if (!gsync()) { leave(); return; }
-            mark(it - 1, 9);
+            const TP* vout = a.outP[a.npc - 1];
             // z into the q cache (q is no longer needed), then r'z
-            // (r'z is summed while z is staged, rows in increasing order per thread)
             rzp = AT(0);
-            stage_sum_pre<NT, TO, TP, TRI_UPPER>(qc, a.PZ, a.ldZ, m2, m2, m2, [&](int j) { return __ldg(a.sg + j); },
-                                             [&](int j, typename Acc<TP>::type v, TP sj) {
-                                                 const TO z = (TO)((AT)sj * (AT)v);
-                                                 rzp = fma((AT)rc[j], (AT)z, rzp);
-                                                 return z;
-                                             });
+            for (int j0 = tid; j0 < m2; j0 += 4 * T) {
+                TP vv[4], sv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int j = j0 + u * T;
+                    vv[u] = j < m2 ? __ldcg(vout + j) : TP(0);
+                    sv[u] = j < m2 ? __ldg(a.sg + j) : TP(0);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int j = j0 + u * T;
+                    if (j < m2) {
+                        const TO z = (TO)((ATP)sv[u] * (ATP)vv[u]);
+                        qc[j] = z;
+                        rzp = fma((AT)rc[j], (AT)z, rzp);
+                    }
+                }
+            }
             rz_new = block_allsum<NT>(rzp, sh);
         } else {
-            rz_new = block_allsum<NT>(rzp, sh);
+            rz_new = rzp;
         }
-        // ---- beta, p = z + beta p (staged as the next P1 input; shared-memory only)
+        // ---- beta, p = z + beta p (staged as the next first-phase input; shared-memory only)
         const AT beta = rz_new / rz;
         rz = rz_new;
         const TO be = (TO)beta;
 #pragma unroll 4
-        for (int j = tid; j < padO_m2; j += kFusedThreads) {
+        for (int j = tid; j < padO_m2; j += T) {
             TO v = TO(0);
             if (j < m2) {
                 TO z;
@@ -813,15 +817,11 @@ __global__ void __launch_bounds__(NT, NT == kSmallBlock ? 2 : 1) pcg_fused_kerne
                 else z = (PC == PC_L_K) ? rc[j] * __ldg(a.Dinv + j) : rc[j];
                 v = fma(be, pcs[j], z);
                 pcs[j] = v;
-                if (j >= own0 && j < own1) pn[j] = v;
             }
             xs[j] = v;
         }
         csync<NT>();
-        mark(it - 1, 10);
-        // swap the double buffers (global copies; the shared caches already hold the new values)
-        TO* t1 = pc; pc = pn; pn = t1;
-        TO* t2 = rcur; rcur = rnext; rnext = t2;
+        mark(it - 1, 9);
     }
     if (blockIdx.x == 0 && tid == 0) {
         a.st->iter = it;
