@@ -36,7 +36,8 @@ WORKLOADS = {
 }
 METRIC = "QPs solved/s at 1e-6 obj err (mixed precision; FP64 path alongside)"
 HEADLINE = 2
-FORM_NAMES = {0: "C', M0 = [K0^-1]_11, C", 1: "B = L^-1[C'; 0] and B'", 2: "C', forward and back solve, C"}
+FORM_NAMES = {0: "C', M0 = [K0^-1]_11, C", 1: "B = L^-1[C'; 0] and B'", 2: "C', forward and back solve, C",
+              3: "V' and V, V = C Z, M0 = Z Z' (rank n - m1)"}
 
 
 def parse():
@@ -55,7 +56,7 @@ def parse():
     ap.add_argument("--profile-pcg", type=int, default=0, metavar="ITERS",
                     help="only factor the QP and run ITERS PCG iterations (a short run for ncu)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"], help="precision of --profile-pcg")
-    ap.add_argument("--pcg-form", type=int, default=0, choices=[0, 1, 2],
+    ap.add_argument("--pcg-form", type=int, default=0, choices=[0, 1, 2, 3],
                     help="--profile-pcg, batch, serving: 0 the implicit K_F product, 1 the W-form")
     ap.add_argument("--workload", default="single", choices=["single", "batch", "serving"],
                     help="batch: the 512 batched QPs through qp_batch_solve; "

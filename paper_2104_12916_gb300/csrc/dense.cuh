@@ -464,6 +464,70 @@ void chol_inv_tc(float* A, long long lda, float* W, long long ldw, int n, int fl
     }
 }
 
+// ------------------------------------------------ pivoted Cholesky, low rank
+// M = Z Z' for a symmetric positive semidefinite M (n x n, FP64) of known rank
+// r: r steps of the outer-product Cholesky, each on the largest remaining
+// diagonal entry (complete diagonal pivoting), Zt = Z' (r x n, row k = column k
+// of Z) so that every thread's reads of a column are coalesced.  One CTA: the
+// steps are sequential, each O(n k).  d: scratch of n doubles.  *rank_out
+// receives the number of steps taken (fewer than r if a pivot falls to
+// rel_floor times the largest diagonal entry).
+__global__ void __launch_bounds__(1024) pivoted_chol_kernel(const double* __restrict__ M, long long ldm, int n, int r,
+                                                            double* __restrict__ Zt, long long ldz,
+                                                            double* __restrict__ d, double rel_floor,
+                                                            int* __restrict__ rank_out) {
+    PCG_COUNT_KERNEL();
+    __shared__ double s_val[32];
+    __shared__ int s_idx[32];
+    __shared__ int s_piv;
+    __shared__ double s_pv, s_dmax;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    for (int i = tid; i < n; i += 1024) d[i] = M[i * ldm + i];
+    __syncthreads();
+    int k = 0;
+    for (; k < r; ++k) {
+        // argmax of the remaining diagonal (ties: the smaller index)
+        double best = -1.0;
+        int bi = -1;
+        for (int i = tid; i < n; i += 1024)
+            if (d[i] > best) { best = d[i]; bi = i; }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ov > best || (ov == best && oi >= 0 && (bi < 0 || oi < bi))) { best = ov; bi = oi; }
+        }
+        if (lane == 0) { s_val[wid] = best; s_idx[wid] = bi; }
+        __syncthreads();
+        if (tid == 0) {
+            double bv = -1.0;
+            int b = -1;
+            for (int w = 0; w < 32; ++w)
+                if (s_val[w] > bv || (s_val[w] == bv && s_idx[w] >= 0 && (b < 0 || s_idx[w] < b))) { bv = s_val[w]; b = s_idx[w]; }
+            if (k == 0) s_dmax = bv;
+            s_piv = (b >= 0 && bv > rel_floor * s_dmax) ? b : -1;
+            s_pv = (s_piv >= 0) ? sqrt(bv) : 0.0;
+        }
+        __syncthreads();
+        const int p = s_piv;
+        if (p < 0) break;
+        const double inv = 1.0 / s_pv;
+        // column k of Z: (M[:, p] - Z[:, 0:k] Z[p, 0:k]') / sqrt(d_p); M symmetric, so row p
+        for (int i = tid; i < n; i += 1024) {
+            double v = M[(long long)p * ldm + i];
+            for (int t = 0; t < k; ++t) v -= Zt[t * ldz + i] * Zt[t * ldz + p];
+            const double z = (i == p) ? s_pv : v * inv;
+            Zt[k * ldz + i] = z;
+        }
+        __syncthreads();
+        for (int i = tid; i < n; i += 1024) {
+            const double z = Zt[k * ldz + i];
+            d[i] = (i == p) ? -1.0 : d[i] - z * z;
+        }
+        __syncthreads();
+    }
+    if (tid == 0) *rank_out = k;
+}
+
 // ------------------------------------------------------------- small helpers
 template <typename T>
 __global__ void transpose_kernel(const T* __restrict__ in, long long ldi, T* __restrict__ out,

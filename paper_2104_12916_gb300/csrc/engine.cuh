@@ -137,7 +137,10 @@ struct Op {
     Mat<TO> Et, EtT;   // Gt R^{-T} = L_S^{-1} A H^{-1} (the (2,1) block of L^{-1}) and its transpose
     Mat<TO> WS, WST;   // L_S^{-1} (lower) and L_S^{-T} (upper)
     Mat<TO> BW, BWT;   // pcg_form 1: B = L^{-1}[C'; 0] = [R^{-T} C'; Et C'] ((n+m1) x m2) and B'
-    Mat<TO> M0;        // [K0^{-1}]_11 = R^{-1} R^{-T} - Et' Et (n x n, symmetric), pcg_form 0
+    Mat<TO> M0;        // [K0^{-1}]_11 = R^{-1} R^{-T} - Et' Et (n x n, symmetric), pcg_form 0 and 3
+    Mat<TO> LV, LVT;   // pcg_form 3: V = C Z (m2 x r) and V', M0 = Z Z', r = rank(M0) = n - m1
+    int lr = 0;        // pcg_form 3: r
+    const TO *cval = nullptr, *ctval = nullptr;   // CSR values of C and C' (QPs created with a CSR C)
     TO *oU = nullptr, *oY, *oZ, *oW;   // persistent kernel: outputs of the operator phases
     TO *px = nullptr, *pr, *pz, *pp, *pq, *pu, *pz1, *pz2, *pt, *py, *prhs, *pD, *pDinv;
     TO *ku, *kw, *ke, *kz1, *kz2, *kt, *ka, *kmb, *wa, *wg;
@@ -176,6 +179,10 @@ public:
 
     // FP64 problem data (masters for residuals and refinement)
     Mat<double> H, A, AT, C, CT;
+    // C in CSR form (qp_create_csr): C (m2 rows) and C' (n rows), indices and FP64 values
+    int *crp = nullptr, *cci = nullptr, *ctrp = nullptr, *ctci = nullptr;
+    double *cval64 = nullptr, *ctval64 = nullptr;
+    long long nnz = 0;
     double *c = nullptr, *b = nullptr, *d = nullptr;
     double h_norm_inf = 0, b_inf = 0, c_inf = 0, d_inf = 0;
 
@@ -293,7 +300,8 @@ public:
             size_t t = 32 * v(cap, es) + 2 * v(n + m1, es);
             if (copyC) t += mat(m2, n, es) + mat(n, m2, es);
             t += 2 * mat(n, n, es);
-            if (o.pcg_form == 0) t += mat(n, n, es);   // M0
+            if (o.pcg_form == 0 || o.pcg_form == 3) t += mat(n, n, es);   // M0
+            if (o.pcg_form == 3) t += mat(m2, std::max(n - m1, 1), es) + mat(std::max(n - m1, 1), m2, es) + mat(n - m1 + 1, n, es) + v(n, es);
             if (m1) t += 2 * mat(m1, m1, es) + 2 * mat(m1, n, es) + 2 * mat(n, m1, es);
             if (o.pcg_form == 1) t += mat(n + m1, m2, es) + mat(m2, n + m1, es);
             t += mat(n, n, es) + 2 * mat(m1, n, es) + mat(m1, m1, es);   // factor scratch
@@ -380,6 +388,15 @@ public:
                 rp = dr; ci = dc; cv = dv;
             }
             csr_scatter_kernel<<<(m2 + 255) / 256, 256, 0, s>>>(m2, n, nnz, rp, ci, cv, C.p, C.ld, csr_bad);
+            // host copies for the C' pattern (built once the pattern is checked)
+            h_rp.resize(m2 + 1);
+            h_ci.resize(nnz);
+            h_cv.resize(nnz);
+            const cudaMemcpyKind back = (ptr_kind == QP_PTR_DEVICE || tmp) ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+            PCG_CK(cudaMemcpyAsync(h_rp.data(), rp, (size_t)(m2 + 1) * 4, back, s));
+            if (nnz) PCG_CK(cudaMemcpyAsync(h_ci.data(), ci, (size_t)nnz * 4, back, s));
+            if (nnz) PCG_CK(cudaMemcpyAsync(h_cv.data(), cv, (size_t)nnz * 8, back, s));
+            wait_stream();
             if (tmp) cudaFreeAsync(tmp, s);
         } else {
             PCG_CK(cudaMemcpy2DAsync(C.p, C.ld * 8, Ch, (size_t)n * 8, (size_t)n * 8, m2, kind, s));
@@ -433,6 +450,7 @@ public:
         else h_info[2] = 0;
         sync_check();
         if (h_info[2] != 0) throw QpError{QP_EINVAL};
+        if (csr) upload_csr();
         h_norm_inf = h_scal[0]; c_inf = h_scal[1]; b_inf = m1 ? h_scal[2] : 0.0; d_inf = h_scal[3];
         float asym;
         std::memcpy(&asym, &h_info[1], sizeof(float));
@@ -448,6 +466,40 @@ public:
         rho_g = vec<double>(n); rho_e = vec<double>(m1); rho_a = vec<double>(m2);
         tx = vec<double>(n); tl = vec<double>(m1); tn = vec<double>(m2);
         sync_check();
+    }
+
+    // C and C' in CSR form on the device (the pattern is checked; C' by a counting
+    // sort on the host: each column's entries in increasing row order).
+    std::vector<int> h_rp, h_ci;
+    std::vector<double> h_cv;
+    void upload_csr() {
+        nnz = (long long)h_ci.size();
+        std::vector<int> trp(n + 1, 0), tci(nnz);
+        std::vector<double> tv(nnz);
+        for (long long k = 0; k < nnz; ++k) ++trp[h_ci[k] + 1];
+        for (int j = 0; j < n; ++j) trp[j + 1] += trp[j];
+        std::vector<int> fill(trp.begin(), trp.end() - 1);
+        for (int i = 0; i < m2; ++i)
+            for (int k = h_rp[i]; k < h_rp[i + 1]; ++k) {
+                const int pos = fill[h_ci[k]]++;
+                tci[pos] = i;
+                tv[pos] = h_cv[k];
+            }
+        const size_t nz = (size_t)std::max(nnz, 1LL);
+        crp = arena.alloc<int>(m2 + 1); cci = arena.alloc<int>(nz);
+        ctrp = arena.alloc<int>(n + 1); ctci = arena.alloc<int>(nz);
+        cval64 = arena.alloc<double>(nz); ctval64 = arena.alloc<double>(nz);
+        PCG_CK(cudaMemcpyAsync(crp, h_rp.data(), (size_t)(m2 + 1) * 4, cudaMemcpyHostToDevice, s));
+        PCG_CK(cudaMemcpyAsync(ctrp, trp.data(), (size_t)(n + 1) * 4, cudaMemcpyHostToDevice, s));
+        if (nnz) {
+            PCG_CK(cudaMemcpyAsync(cci, h_ci.data(), (size_t)nnz * 4, cudaMemcpyHostToDevice, s));
+            PCG_CK(cudaMemcpyAsync(ctci, tci.data(), (size_t)nnz * 4, cudaMemcpyHostToDevice, s));
+            PCG_CK(cudaMemcpyAsync(cval64, h_cv.data(), (size_t)nnz * 8, cudaMemcpyHostToDevice, s));
+            PCG_CK(cudaMemcpyAsync(ctval64, tv.data(), (size_t)nnz * 8, cudaMemcpyHostToDevice, s));
+        }
+        wait_stream();   // the host vectors go away below
+        h_rp.clear(); h_ci.clear(); h_cv.clear();
+        h_rp.shrink_to_fit(); h_ci.shrink_to_fit(); h_cv.shrink_to_fit();
     }
 
     // ------------------------------------------------------------------ factor
@@ -475,7 +527,12 @@ public:
         }
         o.WH.alloc(arena, n, n);
         o.WHT.alloc(arena, n, n);
-        if (opt.pcg_form == 0) o.M0.alloc(arena, n, n);
+        if (opt.pcg_form == 0 || opt.pcg_form == 3) o.M0.alloc(arena, n, n);
+        if (opt.pcg_form == 3) {
+            o.lr = n - m1;
+            o.LV.alloc(arena, m2, std::max(o.lr, 1));
+            o.LVT.alloc(arena, std::max(o.lr, 1), m2);
+        }
         if (m1) {
             o.WS.alloc(arena, m1, m1); o.WST.alloc(arena, m1, m1);
             o.Gt.alloc(arena, m1, n); o.GtT.alloc(arena, n, m1);
@@ -538,8 +595,21 @@ public:
                 if (a.p && b.p) convert2d<double, TO>(a.p, a.ld, b.p, b.ld, a.rows, a.cols, s);
             };
             rnd(o64.WH, o.WH); rnd(o64.WHT, o.WHT); rnd(o64.M0, o.M0);
+            if (opt.pcg_form == 3) {
+                o.lr = o64.lr;
+                rnd(o64.LV, o.LV);
+                rnd(o64.LVT, o.LVT);
+            }
             rnd(o64.WS, o.WS); rnd(o64.WST, o.WST); rnd(o64.Gt, o.Gt); rnd(o64.GtT, o.GtT);
             rnd(o64.Et, o.Et); rnd(o64.EtT, o.EtT);
+            if (crp && !o.cval) {
+                TO* v = arena.alloc<TO>((size_t)std::max(nnz, 1LL));
+                TO* vt = arena.alloc<TO>((size_t)std::max(nnz, 1LL));
+                convert1d<double, TO>((int)nnz, cval64, 1.0, v, s);
+                convert1d<double, TO>((int)nnz, ctval64, 1.0, vt, s);
+                o.cval = v;
+                o.ctval = vt;
+            }
             if (opt.pcg_form == 1) {
                 // B is formed from the FP64 factor and rounded once to FP32, so its entries
                 // carry only their final rounding
@@ -557,6 +627,8 @@ public:
             alloc_op_vectors(o);
             o.CW.p = C.p; o.CW.rows = m2; o.CW.cols = n; o.CW.ld = C.ld;
             o.CWT.p = CT.p; o.CWT.rows = n; o.CWT.cols = m2; o.CWT.ld = CT.ld;
+            o.cval = cval64;
+            o.ctval = ctval64;
         }
         // scratch of the factorization (freed at the end)
         TO *Hw = nullptr, *Aw = nullptr, *G = nullptr, *S = nullptr;
@@ -627,6 +699,31 @@ public:
                 h.B = o.Et.p; h.sbk = o.Et.ld; h.sbj = 1;
                 h.C = o.M0.p; h.ldc = o.M0.ld; h.alpha = TO(-1); h.beta = TO(1);
                 gemm<TO>(h, s);
+            }
+        }
+        if (opt.pcg_form == 3 && o.lr > 0) {
+            // M0 = Z Z' with Z (n x r), r = n - m1 (M0 = R^{-1} (I - P) R^{-T}, P the orthogonal
+            // projector onto the row space of A R^{-1}, of rank m1): pivoted Cholesky, then
+            // V' = Z' C' (r x m2) and V = C Z, so K_F = D + V V' (Sec. 4.3, Lemma 2)
+            const int r = o.lr;
+            TO *Zt = nullptr, *dd = nullptr;
+            galloc(&Zt, (size_t)r * ldn);
+            galloc(&dd, (size_t)n);
+            pivoted_chol_kernel<<<1, 1024, 0, s>>>(o.M0.p, o.M0.ld, n, r, Zt, ldn, dd, 1e-13, d_info + 5);
+            GemmArgs<TO> g{};
+            g.M = r; g.N = m2; g.K = n;
+            g.A = Zt; g.sai = ldn; g.sak = 1;
+            g.B = C.p; g.sbk = 1; g.sbj = C.ld;
+            g.C = o.LVT.p; g.ldc = o.LVT.ld; g.alpha = TO(1); g.beta = TO(0);
+            gemm<TO>(g, s);
+            transpose<TO>(o.LVT.p, o.LVT.ld, o.LV.p, o.LV.ld, r, m2, s);
+            PCG_CK(cudaMemcpyAsync(h_info + 5, d_info + 5, sizeof(int), cudaMemcpyDeviceToHost, s));
+            cudaFreeAsync(Zt, s);
+            cudaFreeAsync(dd, s);
+            wait_stream();
+            if (h_info[5] != r) {
+                if (verbose) std::fprintf(stderr, "  low-rank form: M0 has rank %d, expected %d\n", h_info[5], r);
+                throw QpError{QP_ESINGULAR};
             }
         }
         if (opt.pcg_form == 1) {
@@ -969,6 +1066,12 @@ public:
     static Part mk_part(const void* M, long long ld, int r0, int r1, int cols, int tri, int xoff) {
         Part p;
         p.M = M; p.ld = ld; p.r0 = r0; p.r1 = r1; p.cols = cols; p.tri = tri; p.xoff = xoff;
+        p.rp = nullptr; p.ci = nullptr;
+        return p;
+    }
+    static Part mk_csr(const void* val, const int* rp, const int* ci, int rows, int cols) {
+        Part p = mk_part(val, pad_ld(cols), 0, rows, cols, TRI_NONE, 0);
+        p.rp = rp; p.ci = ci;
         return p;
     }
     static int padc(int v, int ch) { return (v + ch - 1) / ch * ch; }
@@ -995,13 +1098,19 @@ public:
             ph.in_len1 = len1; ph.in_off2 = off2; ph.in_len2 = len2; ph.in_s2 = s2; ph.in_pad = pad;
         };
         const int form = opt.pcg_form;
-        if (form == 1) {
+        if (form == 3) {
+            const int r = o.lr;
+            F.ph[0] = phase({mk_part(o.LVT.p, o.LVT.ld, 0, r, m2, TRI_NONE, 0)}, r);
+            F.ph[1] = phase({mk_part(o.LV.p, o.LV.ld, 0, m2, r, TRI_NONE, 0)}, m2);
+            input(F.ph[1], r, 0, 0, 1.0f, p32(r));
+            F.nop = 2;
+        } else if (form == 1) {
             F.ph[0] = phase({mk_part(o.BW.p, o.BW.ld, 0, n + m1, m2, TRI_NONE, 0)}, n + m1);
             F.ph[1] = phase({mk_part(o.BWT.p, o.BWT.ld, 0, m2, n + m1, TRI_NONE, 0)}, m2);
             input(F.ph[1], n, n, m1, -1.0f, p32(n + m1));
             F.nop = 2;
         } else if (form == 2) {
-            F.ph[0] = phase({mk_part(o.CWT.p, o.CWT.ld, 0, n, m2, TRI_NONE, 0)}, n);
+            F.ph[0] = phase({crp ? mk_csr(o.ctval, ctrp, ctci, n, m2) : mk_part(o.CWT.p, o.CWT.ld, 0, n, m2, TRI_NONE, 0)}, n);
             if (m1) {
                 F.ph[1] = phase({mk_part(o.WH.p, o.WH.ld, 0, n, n, TRI_LOWER, 0),
                                  mk_part(o.Et.p, o.Et.ld, n, n + m1, n, TRI_NONE, 0)}, n + m1);
@@ -1014,14 +1123,14 @@ public:
                 input(F.ph[2], n, 0, 0, 1.0f, p32(n));
             }
             input(F.ph[1], n, 0, 0, 1.0f, p32(n));
-            F.ph[3] = phase({mk_part(o.CW.p, o.CW.ld, 0, m2, n, TRI_NONE, 0)}, m2);
+            F.ph[3] = phase({crp ? mk_csr(o.cval, crp, cci, m2, n) : mk_part(o.CW.p, o.CW.ld, 0, m2, n, TRI_NONE, 0)}, m2);
             input(F.ph[3], n, 0, 0, 1.0f, p32(n));
             F.nop = 4;
         } else {
-            F.ph[0] = phase({mk_part(o.CWT.p, o.CWT.ld, 0, n, m2, TRI_NONE, 0)}, n);
+            F.ph[0] = phase({crp ? mk_csr(o.ctval, ctrp, ctci, n, m2) : mk_part(o.CWT.p, o.CWT.ld, 0, n, m2, TRI_NONE, 0)}, n);
             F.ph[1] = phase({mk_part(o.M0.p, o.M0.ld, 0, n, n, TRI_NONE, 0)}, n);
             input(F.ph[1], n, 0, 0, 1.0f, p32(n));
-            F.ph[2] = phase({mk_part(o.CW.p, o.CW.ld, 0, m2, n, TRI_NONE, 0)}, m2);
+            F.ph[2] = phase({crp ? mk_csr(o.cval, crp, cci, m2, n) : mk_part(o.CW.p, o.CW.ld, 0, m2, n, TRI_NONE, 0)}, m2);
             input(F.ph[2], n, 0, 0, 1.0f, p32(n));
             F.nop = 3;
         }
@@ -1049,23 +1158,42 @@ public:
                 if (isP) F.xs_elems_p = std::max(F.xs_elems_p, (size_t)ph.in_pad);
                 else F.xs_elems_o = std::max(F.xs_elems_o, (size_t)ph.in_pad);
             }
+            // balance rows by weight: 64 per ring item, 1 per row (CSR rows, rows of a
+            // phase without dense chunks); the table records the item prefix
             std::vector<int> pre(ph.rows + 1, 0);
+            std::vector<long long> wpre(ph.rows + 1, 0);
             int ncmax = 1;
             for (int r = 0; r < ph.rows; ++r) {
                 const int it = row_items(ph, CH, r);
                 ncmax = std::max(ncmax, it);
                 pre[r + 1] = pre[r] + it;
+                wpre[r + 1] = wpre[r] + 64LL * it + 1;
             }
             ph.ncmax = ncmax;
             ph.tbl = k * (grid + 1);
-            const long long total = pre[ph.rows];
+            ph.flat = (ph.np == 1 && !ph.p[0].rp && ph.p[0].tri == TRI_NONE && ph.p[0].r0 == 0 &&
+                       ph.p[0].r1 == ph.rows) ? 1 : 0;
+            const long long total = wpre[ph.rows];
             int maxrows = 0;
             for (int b = 0; b <= grid; ++b) {
                 const long long tgt = (total * b + grid / 2) / grid;
                 const int r = (b == grid) ? ph.rows
-                                          : (int)(std::lower_bound(pre.begin(), pre.end(), (int)tgt) - pre.begin());
+                                          : (int)(std::lower_bound(wpre.begin(), wpre.end(), tgt) - wpre.begin());
                 F.tbl[(size_t)ph.tbl + b] = int2{r, pre[r]};
                 if (b > 0) maxrows = std::max(maxrows, r - F.tbl[(size_t)ph.tbl + b - 1].x);
+            }
+            if (ph.flat) {
+                // full-slot chunks over each block's contiguous rows: item prefix per block
+                const long long ld = ph.p[0].ld;
+                int acc = 0;
+                for (int b = 0; b <= grid; ++b) {
+                    int2& t = F.tbl[(size_t)ph.tbl + b];
+                    const int r = t.x;
+                    t.y = acc;
+                    if (b < grid) acc += flat_items(F.tbl[(size_t)ph.tbl + b + 1].x - r, ld, CH);
+                }
+                ph.ncmax = (int)((ld + CH - 1) / CH) + 1;
+                ncmax = ph.ncmax;
             }
             F.spart_bytes = std::max(F.spart_bytes, (size_t)maxrows * ncmax * es);
             // every part's stored row (leading dimension) must lie inside the staged vector
@@ -1127,7 +1255,7 @@ public:
         for (int k = 0; k < F.nop + F.npc; ++k) fa.ph[k] = F.ph[k];
         fa.nop = F.nop; fa.npc = F.npc;
         fa.tbl = d_tbl;
-        if (opt.pcg_form == 1) {
+        if (opt.pcg_form == 1 || opt.pcg_form == 3) {
             fa.out[0] = o.oZ; fa.out[1] = o.oW;
         } else if (opt.pcg_form == 2) {
             fa.out[0] = o.oU; fa.out[1] = o.oZ; fa.out[2] = o.oY; fa.out[3] = o.oW;
@@ -1455,6 +1583,9 @@ public:
         double bo = 2.0 * m2 * n + (double)n * (n + 1) + 2.0 * m1 * n;   // C', the factor's triangles, C
         if (fused && opt.pcg_form == 1) bo = 2.0 * (n + m1) * m2;         // B and B'
         if (fused && opt.pcg_form == 0) bo = 2.0 * m2 * n + (double)n * n;   // C', M0, C
+        if (fused && opt.pcg_form == 3) bo = 2.0 * m2 * (n - m1);             // V' and V
+        if (fused && crp && (opt.pcg_form == 0 || opt.pcg_form == 2))   // C and C' in CSR: values, plus 4-byte indices and row pointers
+            bo += -2.0 * m2 * n + 2.0 * nnz * (1.0 + 4.0 / eo) + (m2 + n + 2) * 4.0 / eo;
         double bp = 0.0;
         if (pc_kind(pc) == PC_H_K) bp = (fused && !pc64) ? (double)m2 * m2 : (double)m2 * (m2 + 1);
         const double vec_el = 12.0 * m2 + 8.0 * n + 4.0 * m1;

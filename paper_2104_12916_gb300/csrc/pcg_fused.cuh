@@ -77,9 +77,11 @@ struct GridBar {
 // SM, so an FP32 path must not touch FP64 arithmetic in its inner loops.)
 template <typename T> struct Acc { using type = T; };
 
-// One row-major matrix of a phase: it contributes to phase rows [r0, r1), its
-// columns are dotted with the staged vector from offset xoff, and chunks outside
-// its stored triangle (relative to its own rows, i = r - r0) are skipped.
+// One matrix of a phase: it contributes to phase rows [r0, r1), its columns are
+// dotted with the staged vector from offset xoff.  Dense (row-major, streamed
+// through the ring; chunks outside its stored triangle, relative to its own rows
+// i = r - r0, are skipped) or CSR (rp, ci and the values M; no ring items: the
+// owning block's thread of a row sums its nonzeros after the dense chunks).
 struct Part {
     const void* M;
     long long ld;     // row stride in elements (a multiple of 32: rows start 128-byte aligned)
@@ -87,6 +89,8 @@ struct Part {
     int cols;
     int tri;          // TRI_NONE, TRI_LOWER (row i: chunks up to i's), TRI_UPPER (from i's)
     int xoff;
+    const int* rp;    // CSR row pointers (rows r1 - r0 + 1) and column indices, or null (dense)
+    const int* ci;
 };
 
 // A phase: up to two parts (stacked rows, or side by side on the same rows),
@@ -101,11 +105,21 @@ struct Phase {
     int tbl;          // offset of this phase's (first row, first item) table: grid + 1 entries
     int in_len1, in_off2, in_len2, in_pad;
     float in_s2;
+    int flat;         // 1: one dense untriangular matrix on rows [0, rows): a block's rows are one
+                      // contiguous range of memory, cut into full-slot chunks that may cross rows
 };
+
+// Rows of a flat phase: local row rl (from the block's first row) spans elements
+// [rl ld, (rl + 1) ld) of the block's range; chunk i spans [i CH, (i + 1) CH).
+__host__ __device__ inline int flat_first_chunk(long long rl, long long ld, int CH) { return (int)(rl * ld / CH); }
+__host__ __device__ inline int flat_row_chunks(long long rl, long long ld, int CH) {
+    return (int)(((rl + 1) * ld - 1) / CH) - (int)(rl * ld / CH) + 1;
+}
+__host__ __device__ inline int flat_items(long long rows, long long ld, int CH) { return (int)((rows * ld + CH - 1) / CH); }
 
 __host__ __device__ inline void part_chunks(const Part& P, int CH, int r, int& c0, int& c1) {
     c0 = c1 = 0;
-    if (r < P.r0 || r >= P.r1) return;
+    if (r < P.r0 || r >= P.r1 || P.rp) return;
     const int nc = (P.cols + CH - 1) / CH;
     const int i = r - P.r0;
     c1 = nc;
@@ -306,8 +320,13 @@ struct RingPos {
     __device__ __forceinline__ void advance(int d, int S) {   // any d >= 0
         slot += d;
         if (slot >= S) {
-            fill += slot / S;
-            slot %= S;
+            if (slot < 2 * S) {
+                slot -= S;
+                ++fill;
+            } else {
+                fill += slot / S;
+                slot %= S;
+            }
         }
     }
 };
@@ -344,10 +363,16 @@ __device__ __forceinline__ bool produce_phase(const Phase& ph, const BlockRange 
     RingPos me = pos;
     Walk w;
     w.CH = CH;
+    const bool flat = ph.flat != 0;
+    const Part& P0 = ph.p[0];
+    const TM* fbase = static_cast<const TM*>(P0.M) + (long long)br.rb0 * P0.ld;   // flat: the block's rows
+    const long long fend = (long long)(br.rb1 - br.rb0) * P0.ld;
     if (i < cnt) {
         me.advance(i, S);
-        w.first_of_row(ph, br.rb0);
-        w.step(ph, i);
+        if (!flat) {
+            w.first_of_row(ph, br.rb0);
+            w.step(ph, i);
+        }
     }
     bool ok = true;
     unsigned polls = 0;
@@ -359,10 +384,25 @@ __device__ __forceinline__ bool produce_phase(const Phase& ph, const BlockRange 
             const int slot = me.slot, fill = me.fill;
             // the slot is free once its previous chunk has been consumed
             if (fill == 0 || mbar_test(&R.empty[slot], (unsigned)((fill - 1) & 1))) {
-                const Part& P = ph.p[w.p];
-                const long long e0 = (long long)w.c * CH;
-                const unsigned bytes = (unsigned)(min((long long)CH, P.ld - e0) * (long long)sizeof(TM));
-                const TM* src = static_cast<const TM*>(P.M) + (long long)(w.row - P.r0) * P.ld + e0;
+                const TM* src;
+                unsigned bytes;
+                if (flat) {
+                    const long long e0 = (long long)i * CH;
+                    src = fbase + e0;
+                    bytes = (unsigned)(min((long long)CH, fend - e0) * (long long)sizeof(TM));
+                    // the slot's next item (one lap ahead) into L2, so that its copy, issued
+                    // once this one is consumed, hits L2
+                    if (i + S < cnt) {
+                        const long long ea = (long long)(i + S) * CH;
+                        const unsigned ba = (unsigned)(min((long long)CH, fend - ea) * (long long)sizeof(TM));
+                        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(fbase + ea), "r"(ba) : "memory");
+                    }
+                } else {
+                    const Part& P = ph.p[w.p];
+                    const long long e0 = (long long)w.c * CH;
+                    bytes = (unsigned)(min((long long)CH, P.ld - e0) * (long long)sizeof(TM));
+                    src = static_cast<const TM*>(P.M) + (long long)(w.row - P.r0) * P.ld + e0;
+                }
                 R.last_fill[slot] = fill;
                 mbar_expect_tx(&R.full[slot], bytes);
                 bulk_g2s(R.buf + (size_t)slot * R.slot_bytes, src, bytes, &R.full[slot]);
@@ -372,7 +412,7 @@ __device__ __forceinline__ bool produce_phase(const Phase& ph, const BlockRange 
                 i += d;
                 if (i < cnt) {
                     me.advance(d, S);
-                    w.step(ph, d);
+                    if (!flat) w.step(ph, d);
                 }
             }
         }
@@ -401,7 +441,53 @@ __device__ __forceinline__ void consume_phase(const Phase& ph, const BlockRange 
     // `warp` on the next lap.  The first owned item is the nearest owned slot.
     int i = cnt;
     for (int s = warp; s < S; s += W) i = min(i, ring_dist(pos.slot, s, S));
-    if (i < cnt) {
+    if (i < cnt && ph.flat) {
+        // flat chunks: split each chunk at the row boundaries it crosses
+        const long long ld = ph.p[0].ld;
+        const long long fend = (long long)(br.rb1 - br.rb0) * ld;
+        RingPos me = pos;
+        me.advance(i, S);
+        while (true) {
+            const int slot = me.slot;
+            if (!mbar_wait(&R.full[slot], (unsigned)(me.fill & 1))) *err = 1;
+            const V* sv = reinterpret_cast<const V*>(R.buf + (size_t)slot * R.slot_bytes);
+            const long long e0 = (long long)i * CH;
+            const long long e1 = min(e0 + CH, fend);
+            long long rl = e0 / ld;
+            TM accs[4];
+            int rows_here = 0;
+            for (long long e = e0; e < e1; ++rl) {
+                const long long se = min(e1, (rl + 1) * ld);
+                const int v0 = (int)((e - e0) / VN), v1 = (int)((se - e0) / VN);
+                // slot vector v holds columns (e0 - rl ld) / VN + v of row rl (exact: both multiples of VN)
+                const int xo = (int)((e0 - rl * ld) / VN);
+                const V* xv = reinterpret_cast<const V*>(xs);
+                TM a0 = TM(0), a1 = TM(0);
+                int v = v0 + lane;
+                for (; v + 32 < v1; v += 64) {
+                    a0 = VT::dot(sv[v], xv[xo + v], a0);
+                    a1 = VT::dot(sv[v + 32], xv[xo + v + 32], a1);
+                }
+                if (v < v1) a0 = VT::dot(sv[v], xv[xo + v], a0);
+                const TM acc = warp_sum(a0 + a1);
+                if (rows_here < 4) accs[rows_here] = acc;
+                else if (lane == 0) spart[rl * ph.ncmax + (i - flat_first_chunk(rl, ld, CH))] = acc;
+                ++rows_here;
+                e = se;
+            }
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(&R.empty[slot]);
+                long long r = e0 / ld;
+                for (int t = 0; t < rows_here && t < 4; ++t, ++r)
+                    spart[r * ph.ncmax + (i - flat_first_chunk(r, ld, CH))] = accs[t];
+            }
+            const int d = (slot + W < S) ? W : warp + S - slot;
+            if (i + d >= cnt) break;
+            i += d;
+            me.advance(d, S);
+        }
+    } else if (i < cnt) {
         RingPos me = pos;
         me.advance(i, S);
         Walk w;
@@ -438,16 +524,24 @@ __device__ __forceinline__ void consume_phase(const Phase& ph, const BlockRange 
     pos.advance(cnt, S);
 }
 
-// Sum each owned row's chunk partials in chunk order and write it to out[row].
+// Sum each owned row's chunk partials in chunk order, add the row's CSR
+// contributions (nonzeros in storage order), and write it to out[row].
 template <typename TM, int NT>
 __device__ __forceinline__ void row_sums(const Phase& ph, const BlockRange br, const TM* __restrict__ spart,
-                                         TM* __restrict__ out, int slot_bytes) {
+                                         TM* __restrict__ out, int slot_bytes, const TM* __restrict__ xs) {
     const int CH = slot_bytes / (int)sizeof(TM);
     for (int r = br.rb0 + (int)threadIdx.x; r < br.rb1; r += Blk<NT>::threads) {
-        const int nk = row_items(ph, CH, r);
+        const int nk = ph.flat ? flat_row_chunks(r - br.rb0, ph.p[0].ld, CH) : row_items(ph, CH, r);
         const TM* sp = spart + (r - br.rb0) * ph.ncmax;
         TM s = TM(0);
         for (int k = 0; k < nk; ++k) s += sp[k];
+        for (int q = 0; q < ph.np; ++q) {
+            const Part& P = ph.p[q];
+            if (!P.rp || r < P.r0 || r >= P.r1) continue;
+            const TM* val = static_cast<const TM*>(P.M);
+            const int k1 = __ldg(P.rp + (r - P.r0) + 1);
+            for (int k = __ldg(P.rp + (r - P.r0)); k < k1; ++k) s = fma(__ldg(val + k), xs[P.xoff + __ldg(P.ci + k)], s);
+        }
         out[r] = s;
     }
 }
@@ -562,12 +656,11 @@ inline size_t fused_smem_bytes(size_t ring_off, int slots, int slot_bytes) {
 template <typename TO, typename TP, int PC>
 __device__ void pcg_producer(const FusedArgs<TO, TP>& a, const BlockRange* brs, const Ring& R) {
     RingPos g;
+    const int nph = a.nop + (PC == PC_H_K ? a.npc : 0);
     while (!*R.stop) {   // (a block may own no chunk of any phase: it polls the stop flag here)
         bool ok = true;
-        for (int k = 0; k < a.nop && ok; ++k) ok = produce_phase<TO>(a.ph[k], brs[k], R, g);
-        if (!ok) break;
-        if (PC == PC_H_K)
-            for (int k = a.nop; k < a.nop + a.npc && ok; ++k) ok = produce_phase<TP>(a.ph[k], brs[k], R, g);
+        for (int k = 0; k < nph && ok; ++k)
+            ok = (k < a.nop) ? produce_phase<TO>(a.ph[k], brs[k], R, g) : produce_phase<TP>(a.ph[k], brs[k], R, g);
         if (!ok) break;
     }
     // drain: every copy issued lands before the block's shared memory goes away
@@ -692,7 +785,7 @@ __global__ void __launch_bounds__(NT, NT == kSmallBlock ? 2 : 1)
             }
             consume_phase<TO, NT>(ph, s_br[k], R, g, xs, spart, &s_err);
             csync<NT>();
-            row_sums<TO, NT>(ph, s_br[k], spart, a.out[k], a.slot_bytes);
+            row_sums<TO, NT>(ph, s_br[k], spart, a.out[k], a.slot_bytes, xs);
             mark(it, 15 + k);
             mark_all(it, k);
             if (!gsync()) { leave(); return; }
@@ -773,7 +866,7 @@ __global__ void __launch_bounds__(NT, NT == kSmallBlock ? 2 : 1)
                 }
                 consume_phase<TP, NT>(ph, s_br[a.nop + k], R, g, xp, spartP, &s_err);
                 csync<NT>();
-                row_sums<TP, NT>(ph, s_br[a.nop + k], spartP, a.outP[k], a.slot_bytes);
+                row_sums<TP, NT>(ph, s_br[a.nop + k], spartP, a.outP[k], a.slot_bytes, xp);
                 mark(it - 1, 19 + k);
                 mark_all(it - 1, a.nop + k);
                 if (!gsync()) { leave(); return; }

@@ -97,7 +97,7 @@ static int create_common(qp_t* out, int n, int m1, int m2, const double* H, cons
     if (opts) o = *opts;
     if (o.precision != QP_PREC_FP32 && o.precision != QP_PREC_FP64) return QP_EINVAL;
     if (o.precond < QP_PC_AUTO || o.precond > QP_PC_NONE) return QP_EINVAL;
-    if (o.pcg_form < 0 || o.pcg_form > 2) return QP_EINVAL;
+    if (o.pcg_form < 0 || o.pcg_form > 3) return QP_EINVAL;
     return guarded([&]() {
         std::unique_ptr<qp_s> h(new qp_s);
         h->eng.reset(new Engine(n, m1, m2, o));

@@ -1,9 +1,13 @@
-"""pcg_form = 1: the persistent kernel applies K_F through B = L^{-1}[C'; 0]
-formed once per QP (two matrix phases instead of four).  The same product, so
-the same bars as the implicit form: reduced solves against the direct solve of
-the explicit K_F (FP64 1e-8, FP32 2e-3; in FP32 mode B is formed from the FP64
-factor and rounded once), and whole IPM solves against the FP64 oracle
-(objective 1e-6, iterations within 2, residuals 1e-8)."""
+"""The other forms of the same K_F product in the persistent kernel:
+  pcg_form 1: through B = L^{-1}[C'; 0] formed once per QP (two matrix phases);
+  pcg_form 2: the forward and the back solve with the stored inverse factor as
+              two phases (four matrix phases);
+  pcg_form 3: the low-rank form K_F = D + V V', V = C Z with M0 = Z Z' of rank
+              n - m1 (Sec. 4.3, Lemma 2), Z from a pivoted Cholesky of M0.
+The same operator, so the same bars as the default form: reduced solves against
+the direct solve of the explicit K_F (FP64 1e-8, FP32 2e-3; in FP32 mode the
+matrices are formed from the FP64 factor and rounded once), and whole IPM solves
+against the FP64 oracle (objective 1e-6, iterations within 2, residuals 1e-8)."""
 import json
 import os
 
@@ -25,20 +29,21 @@ def B():
     return binding
 
 
-def _opts(B, prec, pc=0):
+def _opts(B, prec, pc=0, form=1):
     o = B.qp_opts_default()
-    o.precision, o.precond, o.pcg_form = prec, pc, 1
+    o.precision, o.precond, o.pcg_form = prec, pc, form
     return o
 
 
+@pytest.mark.parametrize("form", [1, 2, 3])
 @pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("pc", [1, 2])
 @pytest.mark.parametrize("shape", [(60, 20, 150), (130, 70, 150), (64, 0, 96), (300, 40, 1100)])
-def test_wform_reduced_solve(B, prec, pc, shape):
+def test_form_reduced_solve(B, prec, pc, shape, form):
     n, m1, m2 = shape
     q = qpgen.dense_qp(n, m1, m2, seed=41)
     D, rhs = qpgen.pcg_inputs(m2, 6, 0.1, 10.0)
-    h = B.QP.from_qpgen(q, _opts(B, prec)).factor()
+    h = B.QP.from_qpgen(q, _opts(B, prec, form=form)).factor()
     tol = 1e-12 if prec == 0 else 1e-5
     dnu = np.zeros(m2)
     st, it, rel = B.qp_pcg_reduced_solve(h.h, D, rhs, dnu, precond=pc, tol=tol, maxit=20000)
@@ -50,12 +55,13 @@ def test_wform_reduced_solve(B, prec, pc, shape):
     h.close()
 
 
+@pytest.mark.parametrize("form", [1, 2, 3])
 @pytest.mark.parametrize("prec", [0, 1])
-def test_wform_ipm_config0(B, prec):
+def test_form_ipm_config0(B, prec, form):
     q = qpgen.config_qp(0)
     with open(os.path.join(HERE, "golden", "oracle_config0.json")) as fh:
         gold = json.load(fh)
-    h = B.QP.from_qpgen(q, _opts(B, prec))
+    h = B.QP.from_qpgen(q, _opts(B, prec, form=form))
     x = np.zeros(q.n)
     st, f, its, _ = B.qp_ipm_solve(h.h, x)
     s = B.qp_get_stats(h.h)
@@ -66,11 +72,12 @@ def test_wform_ipm_config0(B, prec):
     h.close()
 
 
+@pytest.mark.parametrize("form", [1, 3])
 @pytest.mark.parametrize("prec", [0, 1])
-def test_wform_ipm_syqp_and_batch_member(B, prec):
+def test_form_ipm_syqp_and_batch_member(B, prec, form):
     for q in (qpgen.syqp(128, 96, seed=2), qpgen.batch_qp(7)):
         ref = ipm.solve_qp(q, variant="kkt3")
-        h = B.QP.from_qpgen(q, _opts(B, prec))
+        h = B.QP.from_qpgen(q, _opts(B, prec, form=form))
         st, f, its, _ = B.qp_ipm_solve(h.h)
         assert st == B.QP_OK, q.name
         assert abs(f - ref.f) / max(abs(ref.f), 1.0) <= 1e-6, q.name

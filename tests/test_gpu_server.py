@@ -51,16 +51,24 @@ def _solve_alone(B, q, opts):
         B.qp_destroy(h)
 
 
-def test_csr_create_matches_dense_create(B):
+@pytest.mark.parametrize("prec", [0, 1])
+def test_csr_create_matches_dense_create(B, prec):
+    """A CSR C is applied in the persistent kernel as sparse row sums (C' p and
+    C y over the 8 nonzeros of a row), a dense C as streamed rows: the same
+    operator with different rounding, so both reach the oracle's optimum."""
     q = _requests(1, seed0=42)[0]
+    ref = ipm.solve_qp(q, variant="kkt3")
     o = B.qp_opts_default()
-    o.precision = B.QP_PREC_FP64
+    o.precision = prec
     hd = B.QP(np.ascontiguousarray(q.H), q.c, q.A, q.b, np.ascontiguousarray(q.C_dense()), q.d, o)
     st, f, its, x = _solve_alone(B, q, o)
     xd = np.zeros(q.n)
     std, fd, itsd, _ = B.qp_ipm_solve(hd.h, xd)
     assert st == std == B.QP_OK
-    assert np.array_equal(x, xd) and f == fd and its == itsd
+    for ff, ii in ((f, its), (fd, itsd)):
+        assert abs(ff - ref.f) / max(abs(ref.f), 1.0) <= 1e-6
+        assert abs(ii - ref.iters) <= 2
+    assert np.linalg.norm(x - xd) <= 1e-5 * max(1.0, np.linalg.norm(xd))
     hd.close()
 
 
