@@ -467,29 +467,37 @@ void chol_inv_tc(float* A, long long lda, float* W, long long ldw, int n, int fl
 // ------------------------------------------------ pivoted Cholesky, low rank
 // M = Z Z' for a symmetric positive semidefinite M (n x n, FP64) of known rank
 // r: r steps of the outer-product Cholesky, each on the largest remaining
-// diagonal entry (complete diagonal pivoting), Zt = Z' (r x n, row k = column k
-// of Z) so that every thread's reads of a column are coalesced.  One CTA: the
-// steps are sequential, each O(n k).  d: scratch of n doubles.  *rank_out
+// diagonal entry (complete diagonal pivoting); Zt = Z' (r x n, row k = column k
+// of Z) so that every thread's reads of a column are coalesced.  *rank_out
 // receives the number of steps taken (fewer than r if a pivot falls to
-// rel_floor times the largest diagonal entry).
-__global__ void __launch_bounds__(1024) pivoted_chol_kernel(const double* __restrict__ M, long long ldm, int n, int r,
-                                                            double* __restrict__ Zt, long long ldz,
-                                                            double* __restrict__ d, double rel_floor,
-                                                            int* __restrict__ rank_out) {
+// rel_floor times the largest diagonal entry).  d: scratch of n doubles.
+// Spread over a cooperative grid: CTA b owns rows
+// [b n / G, (b + 1) n / G).  One grid barrier per step: before it, every CTA
+// publishes the largest remaining diagonal entry of its rows (value, index) for
+// the step; after it, every CTA reads the G candidates, takes the same pivot p
+// (ties to the smaller index), and computes its rows of column k from Zt rows
+// written in earlier steps.  bar: a zeroed counter; every wait is bounded
+// (2 s of %globaltimer) and a wait that runs out sets *err and ends the kernel.
+__global__ void __launch_bounds__(256) pivoted_chol_grid_kernel(const double* __restrict__ M, long long ldm, int n,
+                                                                int r, double* __restrict__ Zt, long long ldz,
+                                                                double* __restrict__ d, double* __restrict__ cval,
+                                                                int* __restrict__ cidx, unsigned* bar,
+                                                                double rel_floor, int* __restrict__ rank_out,
+                                                                int* __restrict__ err) {
     PCG_COUNT_KERNEL();
-    __shared__ double s_val[32];
-    __shared__ int s_idx[32];
+    __shared__ double s_val[8];
+    __shared__ int s_idx[8];
     __shared__ int s_piv;
     __shared__ double s_pv, s_dmax;
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    for (int i = tid; i < n; i += 1024) d[i] = M[i * ldm + i];
-    __syncthreads();
-    int k = 0;
-    for (; k < r; ++k) {
-        // argmax of the remaining diagonal (ties: the smaller index)
+    __shared__ int s_stop;
+    const int G = gridDim.x, b = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int i0 = (int)((long long)n * b / G), i1 = (int)((long long)n * (b + 1) / G);
+    for (int i = i0 + tid; i < i1; i += 256) d[i] = M[i * ldm + i];
+    unsigned target = 0;
+    auto local_best = [&]() {
         double best = -1.0;
         int bi = -1;
-        for (int i = tid; i < n; i += 1024)
+        for (int i = i0 + tid; i < i1; i += 256)
             if (d[i] > best) { best = d[i]; bi = i; }
         for (int o = 16; o > 0; o >>= 1) {
             const double ov = __shfl_xor_sync(0xffffffffu, best, o);
@@ -500,32 +508,66 @@ __global__ void __launch_bounds__(1024) pivoted_chol_kernel(const double* __rest
         __syncthreads();
         if (tid == 0) {
             double bv = -1.0;
-            int b = -1;
-            for (int w = 0; w < 32; ++w)
-                if (s_val[w] > bv || (s_val[w] == bv && s_idx[w] >= 0 && (b < 0 || s_idx[w] < b))) { bv = s_val[w]; b = s_idx[w]; }
+            int bb = -1;
+            for (int w = 0; w < 8; ++w)
+                if (s_val[w] > bv || (s_val[w] == bv && s_idx[w] >= 0 && (bb < 0 || s_idx[w] < bb))) { bv = s_val[w]; bb = s_idx[w]; }
+            cval[b] = bv;
+            cidx[b] = bb;
+        }
+    };
+    auto grid_barrier = [&]() {
+        __syncthreads();
+        target += G;
+        if (tid == 0) {
+            __threadfence();
+            atomicAdd(bar, 1u);
+            const unsigned long long t0 = [] { unsigned long long t; asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t)); return t; }();
+            unsigned polls = 0;
+            s_stop = 0;
+            while ((int)(*(volatile unsigned*)bar - target) < 0) {
+                if (*(volatile int*)err) { s_stop = 1; break; }
+                if ((++polls & 1023) == 0) {
+                    unsigned long long t;
+                    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+                    if (t - t0 > 2000000000ull) { atomicExch(err, 1); s_stop = 1; break; }
+                }
+            }
+            __threadfence();
+        }
+        __syncthreads();
+        return s_stop == 0;
+    };
+    local_best();
+    int k = 0;
+    for (; k < r; ++k) {
+        if (!grid_barrier()) break;
+        if (tid == 0) {
+            double bv = -1.0;
+            int bb = -1;
+            for (int c = 0; c < G; ++c) {
+                const double v = *(volatile double*)&cval[c];
+                const int ix = *(volatile int*)&cidx[c];
+                if (v > bv || (v == bv && ix >= 0 && (bb < 0 || ix < bb))) { bv = v; bb = ix; }
+            }
             if (k == 0) s_dmax = bv;
-            s_piv = (b >= 0 && bv > rel_floor * s_dmax) ? b : -1;
+            s_piv = (bb >= 0 && bv > rel_floor * s_dmax) ? bb : -1;
             s_pv = (s_piv >= 0) ? sqrt(bv) : 0.0;
         }
         __syncthreads();
         const int p = s_piv;
-        if (p < 0) break;
+        if (p < 0) break;   // (every CTA reads the same candidates: all stop here together)
         const double inv = 1.0 / s_pv;
-        // column k of Z: (M[:, p] - Z[:, 0:k] Z[p, 0:k]') / sqrt(d_p); M symmetric, so row p
-        for (int i = tid; i < n; i += 1024) {
+        for (int i = i0 + tid; i < i1; i += 256) {
             double v = M[(long long)p * ldm + i];
-            for (int t = 0; t < k; ++t) v -= Zt[t * ldz + i] * Zt[t * ldz + p];
+            for (int t = 0; t < k; ++t) v -= Zt[t * ldz + i] * __ldcg(Zt + t * ldz + p);
             const double z = (i == p) ? s_pv : v * inv;
             Zt[k * ldz + i] = z;
-        }
-        __syncthreads();
-        for (int i = tid; i < n; i += 1024) {
-            const double z = Zt[k * ldz + i];
             d[i] = (i == p) ? -1.0 : d[i] - z * z;
         }
         __syncthreads();
+        local_best();
     }
-    if (tid == 0) *rank_out = k;
+    if (b == 0 && tid == 0) *rank_out = k;
 }
 
 // ------------------------------------------------------------- small helpers

@@ -413,7 +413,7 @@ public:
         part_f = vec<double>(cap_rows); diag0 = vec<double>(cap_rows);
         st = arena.alloc<PcgState>(1);
         bar = arena.alloc<GridBar>(1);
-        tstamp = arena.alloc<unsigned long long>(128 + 8 * 1024);
+        tstamp = arena.alloc<unsigned long long>(128 + 8 * 1024 + 3 * kTrace);
         d_tcerr = arena.alloc<int>(1);
         d_tbl = arena.alloc<int2>((size_t)kMaxPhases * kTblStride);
         d_scal = vec<double>(16);
@@ -708,8 +708,24 @@ public:
             const int r = o.lr;
             TO *Zt = nullptr, *dd = nullptr;
             galloc(&Zt, (size_t)r * ldn);
-            galloc(&dd, (size_t)n);
-            pivoted_chol_kernel<<<1, 1024, 0, s>>>(o.M0.p, o.M0.ld, n, r, Zt, ldn, dd, 1e-13, d_info + 5);
+            galloc(&dd, (size_t)n + 2 * 1024 + 64);   // d, then the per-CTA candidates and the barrier words
+            int dev = 0, sms = 0, per_sm = 0;
+            PCG_CK(cudaGetDevice(&dev));
+            PCG_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+            PCG_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pivoted_chol_grid_kernel, 256, 0));
+            int G = std::min(std::min(sms * std::max(per_sm, 1), 1024), std::max(1, n / 16));
+            double* cval = dd + n;
+            int* cidx = reinterpret_cast<int*>(cval + 1024);
+            unsigned* pbar = reinterpret_cast<unsigned*>(cidx + 1024);
+            int* perr = reinterpret_cast<int*>(pbar + 4);
+            PCG_CK(cudaMemsetAsync(pbar, 0, 32, s));
+            const double* M0p = o.M0.p;
+            long long ldm0 = o.M0.ld, ldz = ldn;
+            double rel_floor = 1e-13;
+            int* rank_out = d_info + 5;
+            void* args[] = {(void*)&M0p, (void*)&ldm0, (void*)&n, (void*)&r, (void*)&Zt, (void*)&ldz, (void*)&dd,
+                            (void*)&cval, (void*)&cidx, (void*)&pbar, (void*)&rel_floor, (void*)&rank_out, (void*)&perr};
+            PCG_CK(cudaLaunchCooperativeKernel((const void*)pivoted_chol_grid_kernel, G, 256, args, 0, s));
             GemmArgs<TO> g{};
             g.M = r; g.N = m2; g.K = n;
             g.A = Zt; g.sai = ldn; g.sak = 1;
@@ -1057,6 +1073,7 @@ public:
         int nop = 0, npc = 0;
         size_t xs_elems_o = 0, xs_elems_p = 0;   // staged-vector length in TO / TP elements
         size_t spart_bytes = 0;
+        size_t xo_bytes = 0;                      // the block's slice of x
         std::vector<int2> tbl;
     };
     int2* d_tbl = nullptr;                 // device copy of the block tables (kMaxPhases x (1024 + 1))
@@ -1148,6 +1165,7 @@ public:
         // the first phase's input is p (m2, padded); the P_H phases' is Sg r
         F.xs_elems_o = p32(m2);
         F.xs_elems_p = p32(m2);
+        F.xo_bytes = ((size_t)(m2 + grid - 1) / grid * sizeof(TO) + 15) / 16 * 16;
         F.tbl.assign((size_t)(F.nop + F.npc) * (grid + 1), int2{0, 0});
         for (int k = 0; k < F.nop + F.npc; ++k) {
             Phase& ph = F.ph[k];
@@ -1190,7 +1208,7 @@ public:
                     int2& t = F.tbl[(size_t)ph.tbl + b];
                     const int r = t.x;
                     t.y = acc;
-                    if (b < grid) acc += flat_items(F.tbl[(size_t)ph.tbl + b + 1].x - r, ld, CH);
+                    if (b < grid) acc += flat_items(r, F.tbl[(size_t)ph.tbl + b + 1].x, ld, CH);
                 }
                 ph.ncmax = (int)((ld + CH - 1) / CH) + 1;
                 ncmax = ph.ncmax;
@@ -1216,7 +1234,8 @@ public:
     // vector, the three m2-vector caches and the per-row partials (at most kMaxSlots).
     template <typename TO, typename TP>
     int fused_slots(const FusedPlan& F, int slot_bytes) const {
-        const size_t off = fused_ring_offset(fused_spart_offset<TO>(fused_xs_bytes<TO, TP>(F), m2), F.spart_bytes);
+        const size_t sp = fused_spart_offset<TO>(fused_xs_bytes<TO, TP>(F), m2);
+        const size_t off = fused_ring_offset((sp + F.spart_bytes + 15) / 16 * 16, F.xo_bytes);
         const size_t lim = fused_smem_limit();
         const size_t per = slot_bytes + 2 * sizeof(uint64_t) + sizeof(int);
         if (off + 16 + per > lim) return 0;
@@ -1269,10 +1288,17 @@ public:
         fa.st = st; fa.bar = bar;
         fa.tstamp = phase_times ? tstamp : nullptr;
         fa.leave_early = leave_early ? 1 : 0;
+        {   // block 0's chunks of iteration 2 (its items per iteration from the table)
+            int per_it = 0;
+            for (int k = 0; k < F.nop + F.npc; ++k) per_it += F.tbl[(size_t)F.ph[k].tbl + 1].y - F.tbl[(size_t)F.ph[k].tbl].y;
+            fa.trace0 = 2 * per_it;
+            trace_per_it = per_it;
+        }
         auto kern = pcg_fused_kernel<TO, TP, PC, NT>;
         fa.xs_bytes = fused_xs_bytes<TO, TP>(F);
         fa.spart_off = fused_spart_offset<TO>(fa.xs_bytes, m2);
-        fa.ring_off = fused_ring_offset(fa.spart_off, F.spart_bytes);
+        fa.xo_off = (fa.spart_off + F.spart_bytes + 15) / 16 * 16;
+        fa.ring_off = fused_ring_offset(fa.xo_off, F.xo_bytes);
         int per_sm = 0;
         // A QP whose grid covers most of the GPU takes the deepest ring that fits; a
         // small one (batched with others) a shallow ring, so that the blocks of several
@@ -1337,6 +1363,7 @@ public:
         last_fused_grid = grid;
     }
     int last_fused_grid = 0;
+    int trace_per_it = 0;
 
     template <typename TO, typename TP>
     void pcg_run_fused(int kind) {
@@ -1369,7 +1396,33 @@ public:
                 if (hi) std::fprintf(stderr, " ph%d [%.1f, %.1f]", ph, (lo - t[2 * 32]) * 1e-3, (hi - t[2 * 32]) * 1e-3);
             }
             std::fprintf(stderr, "\n");
-            PCG_CK(cudaMemsetAsync(tstamp, 0, t.size() * 8, s));
+            // block 0's chunk trace over iteration 2: copy latency, consumption, issue gaps
+            std::vector<unsigned long long> tr(3 * kTrace);
+            PCG_CK(cudaMemcpyAsync(tr.data(), tstamp + 128 + 8 * 1024, tr.size() * 8, cudaMemcpyDeviceToHost, s));
+            wait_stream();
+            std::vector<double> lat, use, wait_slot;
+            const int nn = std::min(trace_per_it, kTrace);
+            for (int q = 0; q < nn; ++q) {
+                if (!tr[q] || !tr[kTrace + q] || !tr[2 * kTrace + q]) continue;
+                lat.push_back((double)(tr[kTrace + q] - tr[q]) * 1e-3);
+                use.push_back((double)(tr[2 * kTrace + q] - tr[kTrace + q]) * 1e-3);
+            }
+            auto med = [](std::vector<double> v) {
+                if (v.empty()) return 0.0;
+                std::sort(v.begin(), v.end());
+                return v[v.size() / 2];
+            };
+            auto mx = [](const std::vector<double>& v) { return v.empty() ? 0.0 : *std::max_element(v.begin(), v.end()); };
+            std::fprintf(stderr, "  block 0 chunks of iteration 2: %d traced; issue->landed median %.2f max %.2f us; "
+                                 "landed->released median %.2f max %.2f us\n", (int)lat.size(), med(lat), mx(lat), med(use), mx(use));
+            std::fprintf(stderr, "  issue times (us from the first): ");
+            for (int q = 0; q < nn && q < 96; ++q) std::fprintf(stderr, "%.1f ", tr[q] ? (tr[q] - tr[0]) * 1e-3 : -1.0);
+            std::fprintf(stderr, "\n  landed: ");
+            for (int q = 0; q < nn && q < 96; ++q) std::fprintf(stderr, "%.1f ", tr[kTrace + q] ? (tr[kTrace + q] - tr[0]) * 1e-3 : -1.0);
+            std::fprintf(stderr, "\n  released: ");
+            for (int q = 0; q < nn && q < 96; ++q) std::fprintf(stderr, "%.1f ", tr[2 * kTrace + q] ? (tr[2 * kTrace + q] - tr[0]) * 1e-3 : -1.0);
+            std::fprintf(stderr, "\n");
+            PCG_CK(cudaMemsetAsync(tstamp, 0, (128 + 8 * 1024 + 3 * kTrace) * 8, s));
         }
     }
 
@@ -1381,7 +1434,7 @@ public:
             cudaGetDevice(&d);
             cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, d);
             if (optin <= 0) optin = 227 * 1024;
-            return (size_t)optin - 1024;
+            return (size_t)optin - 2048;   // static shared memory of the kernel (scalars), below 2 KB
         }();
         return lim;
     }

@@ -63,6 +63,7 @@ constexpr int kMaxClusterBlocks = 16;             // grids up to this size launc
 constexpr int kMaxPhases = 6;                     // operator phases (pcg_form 2: four) + P_H (one or two)
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s bound on any wait
 constexpr unsigned kBarErr = 0x40000000u;         // error bit of the barrier counter
+constexpr int kNU = 16;                           // m2-vector elements per thread held in registers
 
 // Grid barrier word: a monotonic arrival counter (zeroed before each launch)
 // whose bit 30 records a failure anywhere, so one acquire load tells a polling
@@ -109,13 +110,19 @@ struct Phase {
                       // contiguous range of memory, cut into full-slot chunks that may cross rows
 };
 
-// Rows of a flat phase: local row rl (from the block's first row) spans elements
-// [rl ld, (rl + 1) ld) of the block's range; chunk i spans [i CH, (i + 1) CH).
-__host__ __device__ inline int flat_first_chunk(long long rl, long long ld, int CH) { return (int)(rl * ld / CH); }
-__host__ __device__ inline int flat_row_chunks(long long rl, long long ld, int CH) {
-    return (int)(((rl + 1) * ld - 1) / CH) - (int)(rl * ld / CH) + 1;
+// Rows of a flat phase: row r spans elements [r ld, (r + 1) ld) of the matrix,
+// chunk c spans [c CH, (c + 1) CH) (global offsets, so that the segments of a row
+// -- and every sum -- are the same for any grid); a block copies the chunks that
+// meet its rows, clipped to them.
+__host__ __device__ inline int flat_first_chunk(long long r, long long ld, int CH) { return (int)(r * ld / CH); }
+__host__ __device__ inline int flat_row_chunks(long long r, long long ld, int CH) {
+    return (int)(((r + 1) * ld - 1) / CH) - (int)(r * ld / CH) + 1;
 }
-__host__ __device__ inline int flat_items(long long rows, long long ld, int CH) { return (int)((rows * ld + CH - 1) / CH); }
+// chunks meeting rows [rb0, rb1)
+__host__ __device__ inline int flat_items(long long rb0, long long rb1, long long ld, int CH) {
+    if (rb1 <= rb0) return 0;
+    return (int)((rb1 * ld + CH - 1) / CH) - (int)(rb0 * ld / CH);
+}
 
 __host__ __device__ inline void part_chunks(const Part& P, int CH, int r, int& c0, int& c1) {
     c0 = c1 = 0;
@@ -228,7 +235,18 @@ struct Ring {
     int* last_fill;          // per slot: fill number of the last copy issued, or -1
     volatile int* stop;      // set by the consumers when they leave
     int S;
+    // diagnostics (block 0, PCGIPM_PHASE_TIMES): %globaltimer at issue, landing and
+    // release of the chunks with ring sequence numbers [trace0, trace0 + kTrace)
+    unsigned long long* trace;
+    int trace0;
 };
+constexpr int kTrace = 512;
+__device__ __forceinline__ void trace_mark(const Ring& R, int which, int fill, int slot) {
+    if (R.trace) {
+        const int q = fill * R.S + slot - R.trace0;
+        if (q >= 0 && q < kTrace) R.trace[which * kTrace + q] = gtimer();
+    }
+}
 
 // Named barrier of the consumer threads (the producer warp never joins it).
 template <int NT>
@@ -365,8 +383,9 @@ __device__ __forceinline__ bool produce_phase(const Phase& ph, const BlockRange 
     w.CH = CH;
     const bool flat = ph.flat != 0;
     const Part& P0 = ph.p[0];
-    const TM* fbase = static_cast<const TM*>(P0.M) + (long long)br.rb0 * P0.ld;   // flat: the block's rows
-    const long long fend = (long long)(br.rb1 - br.rb0) * P0.ld;
+    const TM* fbase = static_cast<const TM*>(P0.M);                   // flat: global element offsets
+    const long long fbeg = (long long)br.rb0 * P0.ld, fend = (long long)br.rb1 * P0.ld;
+    const long long fc0 = fbeg / CH;                                    // first chunk meeting the rows
     if (i < cnt) {
         me.advance(i, S);
         if (!flat) {
@@ -387,14 +406,14 @@ __device__ __forceinline__ bool produce_phase(const Phase& ph, const BlockRange 
                 const TM* src;
                 unsigned bytes;
                 if (flat) {
-                    const long long e0 = (long long)i * CH;
+                    const long long e0 = max(fbeg, (fc0 + i) * CH), e1 = min(fend, (fc0 + i + 1) * CH);
                     src = fbase + e0;
-                    bytes = (unsigned)(min((long long)CH, fend - e0) * (long long)sizeof(TM));
+                    bytes = (unsigned)((e1 - e0) * (long long)sizeof(TM));
                     // the slot's next item (one lap ahead) into L2, so that its copy, issued
                     // once this one is consumed, hits L2
                     if (i + S < cnt) {
-                        const long long ea = (long long)(i + S) * CH;
-                        const unsigned ba = (unsigned)(min((long long)CH, fend - ea) * (long long)sizeof(TM));
+                        const long long ea = max(fbeg, (fc0 + i + S) * CH), eb = min(fend, (fc0 + i + S + 1) * CH);
+                        const unsigned ba = (unsigned)((eb - ea) * (long long)sizeof(TM));
                         asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(fbase + ea), "r"(ba) : "memory");
                     }
                 } else {
@@ -404,6 +423,7 @@ __device__ __forceinline__ bool produce_phase(const Phase& ph, const BlockRange 
                     src = static_cast<const TM*>(P.M) + (long long)(w.row - P.r0) * P.ld + e0;
                 }
                 R.last_fill[slot] = fill;
+                trace_mark(R, 0, fill, slot);
                 mbar_expect_tx(&R.full[slot], bytes);
                 bulk_g2s(R.buf + (size_t)slot * R.slot_bytes, src, bytes, &R.full[slot]);
                 // next owned slot: the lane's other slot, else the same slot one lap later
@@ -444,16 +464,18 @@ __device__ __forceinline__ void consume_phase(const Phase& ph, const BlockRange 
     if (i < cnt && ph.flat) {
         // flat chunks: split each chunk at the row boundaries it crosses
         const long long ld = ph.p[0].ld;
-        const long long fend = (long long)(br.rb1 - br.rb0) * ld;
+        const long long fbeg = (long long)br.rb0 * ld, fend = (long long)br.rb1 * ld;
+        const long long fc0 = fbeg / CH;
         RingPos me = pos;
         me.advance(i, S);
         while (true) {
             const int slot = me.slot;
             if (!mbar_wait(&R.full[slot], (unsigned)(me.fill & 1))) *err = 1;
+            if (lane == 0) trace_mark(R, 1, me.fill, slot);
             const V* sv = reinterpret_cast<const V*>(R.buf + (size_t)slot * R.slot_bytes);
-            const long long e0 = (long long)i * CH;
-            const long long e1 = min(e0 + CH, fend);
-            long long rl = e0 / ld;
+            const long long c = fc0 + i;                         // global chunk
+            const long long e0 = max(fbeg, c * CH), e1 = min(fend, (c + 1) * CH);
+            long long rl = e0 / ld;                              // global row
             TM accs[4];
             int rows_here = 0;
             for (long long e = e0; e < e1; ++rl) {
@@ -471,16 +493,17 @@ __device__ __forceinline__ void consume_phase(const Phase& ph, const BlockRange 
                 if (v < v1) a0 = VT::dot(sv[v], xv[xo + v], a0);
                 const TM acc = warp_sum(a0 + a1);
                 if (rows_here < 4) accs[rows_here] = acc;
-                else if (lane == 0) spart[rl * ph.ncmax + (i - flat_first_chunk(rl, ld, CH))] = acc;
+                else if (lane == 0) spart[(rl - br.rb0) * ph.ncmax + (int)(c - flat_first_chunk(rl, ld, CH))] = acc;
                 ++rows_here;
                 e = se;
             }
             __syncwarp();
             if (lane == 0) {
                 mbar_arrive(&R.empty[slot]);
+                trace_mark(R, 2, me.fill, slot);
                 long long r = e0 / ld;
                 for (int t = 0; t < rows_here && t < 4; ++t, ++r)
-                    spart[r * ph.ncmax + (i - flat_first_chunk(r, ld, CH))] = accs[t];
+                    spart[(r - br.rb0) * ph.ncmax + (int)(c - flat_first_chunk(r, ld, CH))] = accs[t];
             }
             const int d = (slot + W < S) ? W : warp + S - slot;
             if (i + d >= cnt) break;
@@ -498,6 +521,7 @@ __device__ __forceinline__ void consume_phase(const Phase& ph, const BlockRange 
             const Part& P = ph.p[w.p];
             const int slot = me.slot;
             if (!mbar_wait(&R.full[slot], (unsigned)(me.fill & 1))) *err = 1;
+            if (lane == 0) trace_mark(R, 1, me.fill, slot);
             const V* sv = reinterpret_cast<const V*>(R.buf + (size_t)slot * R.slot_bytes);
             const V* xv = reinterpret_cast<const V*>(xs + P.xoff + w.c * CH);
             // vectors copied into the slot (the row's padding columns are zeros)
@@ -511,7 +535,10 @@ __device__ __forceinline__ void consume_phase(const Phase& ph, const BlockRange 
             }
             if (v < vend) a0 = VT::dot(sv[v], xv[v], a0);
             __syncwarp();
-            if (lane == 0) mbar_arrive(&R.empty[slot]);
+            if (lane == 0) {
+                mbar_arrive(&R.empty[slot]);
+                trace_mark(R, 2, me.fill, slot);
+            }
             TM acc = warp_sum(a0 + a1);
             if (lane == 0) spart[(w.row - br.rb0) * ph.ncmax + w.k] = acc;
             const int d = (slot + W < S) ? W : warp + S - slot;
@@ -531,7 +558,7 @@ __device__ __forceinline__ void row_sums(const Phase& ph, const BlockRange br, c
                                          TM* __restrict__ out, int slot_bytes, const TM* __restrict__ xs) {
     const int CH = slot_bytes / (int)sizeof(TM);
     for (int r = br.rb0 + (int)threadIdx.x; r < br.rb1; r += Blk<NT>::threads) {
-        const int nk = ph.flat ? flat_row_chunks(r - br.rb0, ph.p[0].ld, CH) : row_items(ph, CH, r);
+        const int nk = ph.flat ? flat_row_chunks(r, ph.p[0].ld, CH) : row_items(ph, CH, r);
         const TM* sp = spart + (r - br.rb0) * ph.ncmax;
         TM s = TM(0);
         for (int k = 0; k < nk; ++k) s += sp[k];
@@ -628,12 +655,14 @@ struct FusedArgs {
     GridBar* bar;      // zeroed before the launch
     size_t xs_bytes;   // bytes of the staged-vector region of shared memory (16-byte multiple)
     size_t spart_off;  // byte offset of the per-row chunk partials
+    size_t xo_off;     // byte offset of the block's slice of x (ceil(m2 / grid) elements)
     size_t ring_off;   // byte offset of the slot ring (128-byte aligned)
     int slots;         // ring depth S
     int slot_bytes;    // bytes of one slot (a multiple of 16)
     unsigned long long* tstamp;   // optional: %globaltimer marks of block 0 (4 iterations x 32) and
                                   // every block's phase ends of iteration 2 (8 x grid, after 128)
     int leave_early;              // failure-detection test: block 0 leaves before its first grid barrier
+    int trace0;                   // first ring sequence number of block 0's chunk trace (see Ring)
 };
 
 // Shared-memory layout of the persistent kernel: staged vector, three m2-vector
@@ -694,6 +723,8 @@ __global__ void __launch_bounds__(NT, NT == kSmallBlock ? 2 : 1)
     R.empty = R.full + R.S;
     R.last_fill = reinterpret_cast<int*>(R.empty + R.S);
     R.stop = reinterpret_cast<volatile int*>(R.last_fill + R.S);
+    R.trace = (a.tstamp != nullptr && blockIdx.x == 0) ? a.tstamp + 128 + 8 * 1024 : nullptr;
+    R.trace0 = a.trace0;
     using AT = typename Acc<TO>::type;
     using ATP = typename Acc<TP>::type;
     __shared__ AT sh[40];
@@ -727,9 +758,12 @@ __global__ void __launch_bounds__(NT, NT == kSmallBlock ? 2 : 1)
     // ------------------------------------------------------------ consumers
     TO* spart = reinterpret_cast<TO*>(pcg_smem + a.spart_off);
     TP* spartP = reinterpret_cast<TP*>(pcg_smem + a.spart_off);
-    // slice of the m2-vectors this block owns for writes
+    // slice of x this block owns: accumulated in shared memory (x = 0 at entry),
+    // written to global memory when the solve ends
     const int per = (m2 + nblocks - 1) / nblocks;
     const int own0 = blockIdx.x * per, own1 = min(m2, own0 + per);
+    TO* xo = reinterpret_cast<TO*>(pcg_smem + a.xo_off);
+    for (int j = tid; j < per; j += T) xo[j] = TO(0);
     // staged m2-vectors are padded to 32 elements (the leading dimension of C' and P~^{-1})
     const int padO_m2 = ((m2 + 31) / 32) * 32, padP_m2 = padO_m2;
     const bool stamp = a.tstamp != nullptr && blockIdx.x == 0 && tid == 0;
@@ -793,27 +827,31 @@ __global__ void __launch_bounds__(NT, NT == kSmallBlock ? 2 : 1)
         }
 
         // ---- (a10) q = D p + w (cached), alpha = r'z / p'q, x += alpha p, r -= alpha q
-        // (p'q is summed while q is staged: each thread takes its rows in increasing order)
+        // Each thread takes the elements j = tid + u T, all of a pass's global loads issued
+        // before any is used (one round of latency per pass); sums in increasing u.
         AT pq = AT(0);
         {
             const TO* w = a.out[a.nop - 1];
-            for (int j0 = tid; j0 < m2; j0 += 4 * T) {
-                TO wv[4], dv[4];
+            TO wv[kNU], dv[kNU];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int j = j0 + u * T;
-                    wv[u] = j < m2 ? __ldcg(w + j) : TO(0);
-                    dv[u] = j < m2 ? __ldg(a.D + j) : TO(0);
-                }
+            for (int u = 0; u < kNU; ++u) {
+                const int j = tid + u * T;
+                wv[u] = j < m2 ? __ldcg(w + j) : TO(0);
+                dv[u] = j < m2 ? __ldg(a.D + j) : TO(0);
+            }
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int j = j0 + u * T;
-                    if (j < m2) {
-                        const TO q = (TO)fma((AT)dv[u], (AT)pcs[j], (AT)wv[u]);
-                        qc[j] = q;
-                        pq = fma((AT)pcs[j], (AT)q, pq);
-                    }
+            for (int u = 0; u < kNU; ++u) {
+                const int j = tid + u * T;
+                if (j < m2) {
+                    const TO q = (TO)fma((AT)dv[u], (AT)pcs[j], (AT)wv[u]);
+                    qc[j] = q;
+                    pq = fma((AT)pcs[j], (AT)q, pq);
                 }
+            }
+            for (int j = tid + kNU * T; j < m2; j += T) {
+                const TO q = (TO)fma((AT)__ldg(a.D + j), (AT)pcs[j], (AT)__ldcg(w + j));
+                qc[j] = q;
+                pq = fma((AT)pcs[j], (AT)q, pq);
             }
         }
         pq = block_allsum<NT>(pq, sh);
@@ -823,25 +861,41 @@ __global__ void __launch_bounds__(NT, NT == kSmallBlock ? 2 : 1)
         const AT alpha = rz / pq;
         const TO al = (TO)alpha;
         AT rrp = AT(0), rzp = AT(0);
-#pragma unroll 4
-        for (int j = tid; j < padO_m2; j += T) {
-            if (j >= m2) {
-                if (PC == PC_H_K) { if (j < padP_m2) xp[j] = TP(0); } else xs[j] = TO(0);
-                continue;
+        {
+            // the preconditioner's diagonal factor: 1/D (P_L) or the Jacobi scaling Sg (P_H)
+            const TO* dz = (PC == PC_L_K) ? a.Dinv : nullptr;
+            TO zv[kNU];
+            TP gv[kNU];
+#pragma unroll
+            for (int u = 0; u < kNU; ++u) {
+                const int j = tid + u * T;
+                zv[u] = (PC == PC_L_K && j < m2) ? __ldg(dz + j) : TO(1);
+                gv[u] = (PC == PC_H_K && j < m2) ? __ldg(a.sg + j) : TP(0);
             }
-            const TO rn = fma(-al, qc[j], rc[j]);
-            rc[j] = rn;
-            rrp = fma((AT)rn, (AT)rn, rrp);
-            if (j >= own0 && j < own1) a.x[j] = fma(al, pcs[j], a.x[j]);
-            if (PC == PC_H_K) {
-                xp[j] = (TP)((AT)rn * (AT)__ldg(a.sg + j));
-            } else {
-                const TO z = (PC == PC_L_K) ? rn * __ldg(a.Dinv + j) : rn;
-                rzp = fma((AT)rn, (AT)z, rzp);
+            auto update = [&](int j, TO dzj, TP sgj) {
+                const TO rn = fma(-al, qc[j], rc[j]);
+                rc[j] = rn;
+                rrp = fma((AT)rn, (AT)rn, rrp);
+                if (j >= own0 && j < own1) xo[j - own0] = fma(al, pcs[j], xo[j - own0]);
+                if (PC == PC_H_K) {
+                    xp[j] = (TP)((AT)rn * (AT)sgj);
+                } else {
+                    const TO z = rn * dzj;   // (dzj = 1 without a preconditioner)
+                    xs[j] = z;               // z for the p update below (xs is free until then)
+                    rzp = fma((AT)rn, (AT)z, rzp);
+                }
+            };
+#pragma unroll
+            for (int u = 0; u < kNU; ++u) {
+                const int j = tid + u * T;
+                if (j < m2) update(j, zv[u], gv[u]);
             }
+            for (int j = tid + kNU * T; j < m2; j += T)
+                update(j, (PC == PC_L_K) ? __ldg(dz + j) : TO(1), (PC == PC_H_K) ? __ldg(a.sg + j) : TP(0));
         }
-        if (PC == PC_H_K)
-            for (int j = padO_m2 + tid; j < padP_m2; j += T) xp[j] = TP(0);
+        for (int j = m2 + tid; j < padO_m2; j += T) {
+            if (PC == PC_H_K) xp[j] = TP(0); else xs[j] = TO(0);
+        }
         if (PC == PC_H_K) {
             rr = block_allsum<NT>(rrp, sh);
         } else {
@@ -875,22 +929,27 @@ __global__ void __launch_bounds__(NT, NT == kSmallBlock ? 2 : 1)
             const TP* vout = a.outP[a.npc - 1];
             // z into the q cache (q is no longer needed), then r'z
             rzp = AT(0);
-            for (int j0 = tid; j0 < m2; j0 += 4 * T) {
-                TP vv[4], sv[4];
+            {
+                TP vv[kNU], sv[kNU];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int j = j0 + u * T;
+                for (int u = 0; u < kNU; ++u) {
+                    const int j = tid + u * T;
                     vv[u] = j < m2 ? __ldcg(vout + j) : TP(0);
                     sv[u] = j < m2 ? __ldg(a.sg + j) : TP(0);
                 }
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int j = j0 + u * T;
+                for (int u = 0; u < kNU; ++u) {
+                    const int j = tid + u * T;
                     if (j < m2) {
                         const TO z = (TO)((ATP)sv[u] * (ATP)vv[u]);
                         qc[j] = z;
                         rzp = fma((AT)rc[j], (AT)z, rzp);
                     }
+                }
+                for (int j = tid + kNU * T; j < m2; j += T) {
+                    const TO z = (TO)((ATP)__ldg(a.sg + j) * (ATP)__ldcg(vout + j));
+                    qc[j] = z;
+                    rzp = fma((AT)rc[j], (AT)z, rzp);
                 }
             }
             rz_new = block_allsum<NT>(rzp, sh);
@@ -905,9 +964,7 @@ __global__ void __launch_bounds__(NT, NT == kSmallBlock ? 2 : 1)
         for (int j = tid; j < padO_m2; j += T) {
             TO v = TO(0);
             if (j < m2) {
-                TO z;
-                if (PC == PC_H_K) z = qc[j];
-                else z = (PC == PC_L_K) ? rc[j] * __ldg(a.Dinv + j) : rc[j];
+                const TO z = (PC == PC_H_K) ? qc[j] : xs[j];
                 v = fma(be, pcs[j], z);
                 pcs[j] = v;
             }
@@ -916,6 +973,8 @@ __global__ void __launch_bounds__(NT, NT == kSmallBlock ? 2 : 1)
         csync<NT>();
         mark(it - 1, 9);
     }
+    csync<NT>();
+    for (int j = own0 + tid; j < own1; j += T) a.x[j] = xo[j - own0];
     if (blockIdx.x == 0 && tid == 0) {
         a.st->iter = it;
         a.st->rr = (double)rr;
