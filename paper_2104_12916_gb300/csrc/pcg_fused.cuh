@@ -409,13 +409,6 @@ __device__ __forceinline__ bool produce_phase(const Phase& ph, const BlockRange 
                     const long long e0 = max(fbeg, (fc0 + i) * CH), e1 = min(fend, (fc0 + i + 1) * CH);
                     src = fbase + e0;
                     bytes = (unsigned)((e1 - e0) * (long long)sizeof(TM));
-                    // the slot's next item (one lap ahead) into L2, so that its copy, issued
-                    // once this one is consumed, hits L2
-                    if (i + S < cnt) {
-                        const long long ea = max(fbeg, (fc0 + i + S) * CH), eb = min(fend, (fc0 + i + S + 1) * CH);
-                        const unsigned ba = (unsigned)((eb - ea) * (long long)sizeof(TM));
-                        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(fbase + ea), "r"(ba) : "memory");
-                    }
                 } else {
                     const Part& P = ph.p[w.p];
                     const long long e0 = (long long)w.c * CH;
