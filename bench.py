@@ -36,7 +36,7 @@ WORKLOADS = {
 }
 METRIC = "QPs solved/s at 1e-6 obj err (mixed precision; FP64 path alongside)"
 HEADLINE = 2
-FORM_NAMES = {0: "C', M0 = [K0^-1]_11, C", 1: "B = L^-1[C'; 0] and B'", 2: "C', forward and back solve, C",
+FORM_NAMES = {-1: "auto", 0: "C', M0 = [K0^-1]_11, C", 1: "B = L^-1[C'; 0] and B'", 2: "C', forward and back solve, C",
               3: "V' and V, V = C Z, M0 = Z Z' (rank n - m1)"}
 
 
@@ -56,8 +56,8 @@ def parse():
     ap.add_argument("--profile-pcg", type=int, default=0, metavar="ITERS",
                     help="only factor the QP and run ITERS PCG iterations (a short run for ncu)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"], help="precision of --profile-pcg")
-    ap.add_argument("--pcg-form", type=int, default=0, choices=[0, 1, 2, 3],
-                    help="--profile-pcg, batch, serving: 0 the implicit K_F product, 1 the W-form")
+    ap.add_argument("--pcg-form", type=int, default=-1, choices=[-1, 0, 1, 2, 3],
+                    help="--profile-pcg, batch, serving: -1 auto, 0 C' M0 C, 1 the W-form, 2 the factor, 3 low rank")
     ap.add_argument("--workload", default="single", choices=["single", "batch", "serving"],
                     help="batch: the 512 batched QPs through qp_batch_solve; "
                          "serving: a Poisson stream of the served workload's QPs through qp_server_*")
@@ -176,7 +176,7 @@ class ClockSampler:
 
 # ------------------------------------------------------------------ our solver
 STAT_KEYS = ("newton_solves", "refine_sweeps", "op64_switch_iter", "pc64_switch_iter", "pc_switch_iter",
-             "op64_solves", "t_factor_ms", "t_pcg_ms", "t_precond_ms", "t_solve_ms")
+             "op64_solves", "pcg_form_used", "t_factor_ms", "t_pcg_ms", "t_precond_ms", "t_solve_ms")
 
 
 def per_solve(r):
@@ -202,7 +202,7 @@ class Solver:
         self.args = (t(q.H), t(q.c), t(q.A), t(q.b), t(q.C), t(q.d))
         self.x = torch.zeros(q.n, dtype=torch.float64, device=dev)
 
-    def opts(self, prec, form=0):
+    def opts(self, prec, form=-1):
         o = self.B.qp_opts_default()
         o.precision = prec
         o.pcg_form = form
@@ -212,7 +212,7 @@ class Solver:
     def ok(self, r):
         return r["status"] == 0 and abs(r["f"] - self.gold["f"]) / max(abs(self.gold["f"]), 1.0) <= 1e-6
 
-    def step(self, prec, out, form=0):
+    def step(self, prec, out, form=-1):
         B = self.B
         h = B.qp_create(*self.args, self.opts(prec, form))
         try:
@@ -262,7 +262,7 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def timed(sv, prec, steps, warmup, form=0):
+    def timed(sv, prec, steps, warmup, form=-1):
         res = []
         for _ in range(warmup):
             sv.step(prec, [], form)
@@ -306,11 +306,13 @@ def run_ours(args):
         return {"form": FORM_NAMES[form], "us": round(ms * 1e3, 2), "algorithmic_MB": round(by / 1e6, 2),
                 "GBps": round(gbs, 1), "frac": round(gbs / peak, 4)}
 
-    pcg_it = {f"config{main.cfg}_form{f}": iteration_entry(main, f) for f in (0, 2, 1)}
-    head = pcg_it[f"config{main.cfg}_form0"]
+    form_used = res[-1]["stats"]["pcg_form_used"] if res else 0
+    pcg_it = {f"config{main.cfg}_form{f}": iteration_entry(main, f) for f in (form_used, 0, 2, 1, 3)
+              if f != 3 or 2 * main.qp.m1 >= main.qp.n}
+    head = pcg_it[f"config{main.cfg}_form{form_used}"]
     traffic = None
     try:
-        with open(os.path.join(ROOT, "profiles", f"pcg_iteration_traffic_config{main.cfg}.json")) as fh:
+        with open(os.path.join(ROOT, "profiles", f"pcg_iteration_traffic_config{main.cfg}_form{form_used}.json")) as fh:
             tr = json.load(fh)
         if tr.get("source_hash") == source_hash():
             traffic = tr.get("dram_bytes_per_iteration")
@@ -319,9 +321,10 @@ def run_ours(args):
     pc_name = "P_L (few degrees of freedom)" if main.qp.m1 * 2 >= main.qp.n else "P_H (few equalities)"
     roofline = {"bound": "hbm", "achieved": head["GBps"], "peak": peak, "unit": "GB/s", "frac": head["frac"],
                 "traffic": traffic,
-                "kernel": f"one PCG iteration on K_F, {pc_name}: C'p, M0 u, C y + D p, update"
-                          + (", P_H^-1 r" if main.qp.m1 * 2 < main.qp.n else "")
-                          + f": {head['algorithmic_MB']} MB algorithmic, {head['us']} us",
+                "kernel": f"one PCG iteration on K_F ({FORM_NAMES[form_used]}), {pc_name}"
+                          + f": {head['algorithmic_MB']} MB algorithmic, {head['us']} us"
+                          + (" (the operator fits in L2: the iteration is bound by its grid barriers"
+                             " and vector step, not by HBM)" if head["algorithmic_MB"] < 100 else ""),
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback"}
 
     # ---- end to end through host buffers (H2D of the inputs and D2H of x inside)
@@ -364,7 +367,7 @@ def run_ours(args):
             "fp64": {"value": round(sum(ok1d) / (t1d / 1e3), 4), "unit": "QPs/s", "ms_per_step": round(t1d / 2, 1),
                      "solved": f"{sum(ok1d)}/{len(ok1d)}", "ipm_iters": [r["ipm"] for r in r1d],
                      "per_solve": per_solve(r1d[-1])}}
-        for f in (0, 2, 1):
+        for f in (0, 2, 1) + ((3,) if 2 * other.qp.m1 >= other.qp.n else ()):
             pcg_it[f"config{other.cfg}_form{f}"] = iteration_entry(other, f)
         del other
         torch.cuda.synchronize()
@@ -383,7 +386,7 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": WORKLOADS[main.cfg],
                        "precision": "mixed (FP32 operator and P_H, FP64 refinement and step logic)",
-                       "preconditioner": "auto -> " + pc_name, "pcg_form": FORM_NAMES[0],
+                       "preconditioner": "auto -> " + pc_name, "pcg_form": "auto -> " + FORM_NAMES[form_used],
                        "parallelism": f"replicas x{world}",
                        "l2": "flushed between timed steps (256 MB write, untimed)"},
             "solved": f"{sum(ok)}/{len(ok)} per rank",
@@ -477,7 +480,7 @@ BATCH_WORKLOAD = ("512 dense QPs, n uniform [64,512], m_eq uniform [0.1n,0.5n], 
                   "Lambda log-uniform [1e-2,1e2], seeds 1e6+i")
 
 
-def batch_measure(B, local, qps, concurrency, pcg_form=0, check_n=160, precs=None):
+def batch_measure(B, local, qps, concurrency, pcg_form=-1, check_n=160, precs=None):
     """The batched workload through qp_batch_solve: every QP created from host
     buffers, solved with many in flight (each QP's persistent PCG kernel on 8-16
     blocks launched as one cluster, host waits yielding), the solution read back.
@@ -562,7 +565,7 @@ SERVING_WORKLOAD = ("served stream: n log-uniform [64,4096], m_eq = n U(0.05,0.9
                     "C CSR 8 nnz/row, Lambda log-uniform [1e-2,1e2], Poisson arrivals")
 
 
-def serving_measure(B, local, qps, arrive, budget_gb, slots, pcg_form=0, check_n=256):
+def serving_measure(B, local, qps, arrive, budget_gb, slots, pcg_form=-1, check_n=256):
     """A Poisson stream through qp_server_*: requests are submitted at their
     arrival times (host buffers: the submission copies them, the server moves them
     to the device when it admits them), results polled as they complete.

@@ -89,6 +89,9 @@ enum qp_pcg_mode {
 
 enum qp_ptr_kind { QP_PTR_HOST = 0, QP_PTR_DEVICE = 1 };
 
+/* qp_opts.pcg_form: -1 lets qp_create choose (see qp_opts.pcg_form). */
+enum qp_pcg_form { QP_FORM_AUTO = -1 };
+
 typedef struct qp_s *qp_t;   /* opaque; owns every device buffer it allocates */
 
 typedef struct {
@@ -123,8 +126,24 @@ typedef struct {
                              phases, 2 m2 n + n^2 + 2 m1 n elements).  1: the same product through
                              B = L^{-1}[C'; 0] = [R^{-T} C'; Et C'], formed once per QP:
                              K_F p = D p + B1'(B1 p) - B2'(B2 p) (two matrix phases; 2 (n + m1) m2
-                             elements).  All three are the same operator; the per-phase kernels
-                             (pcg_check_every < 0) always use the two triangular solves. */
+                             elements).  3: the low-rank form (Sec. 4.3, Lemma 2: M0 has rank
+                             r = n - m1): M0 = Z Z' by r steps of a pivoted Cholesky once per QP,
+                             V = C Z, K_F p = D p + V (V' p) (two matrix phases, 2 m2 r elements;
+                             QP_ESINGULAR if M0's numerical rank is below r; a handle that chose
+                             it by QP_FORM_AUTO takes form 0 instead).  All four are the
+                             same operator; the per-phase kernels (pcg_check_every < 0) always use
+                             the two triangular solves.  QP_FORM_AUTO (default): 3 when 2 m1 >= n
+                             and 1 <= n - m1 <= 1024 (few degrees of freedom), else 0; the choice
+                             is reported in qp_stats.pcg_form_used. */
+    int factor_tc;        /* QP_PREC_FP32 with pcg_form 0 or 2: 1 forms the FP32 operator's K0 factor
+                             (and M0) in FP32 storage with FP64 diagonal-block pivots and the dense
+                             contractions -- the blocked Cholesky's trailing and inverse updates,
+                             G = A R^{-1}, A H^{-1} A', L_S^{-1} G, Et, M0 -- on the tcgen05 tensor
+                             cores (FP32-accurate 3xTF32 splits); a pivot below 1e-6 of its diagonal
+                             entry falls back to the default.  0 (default): the factor is formed in
+                             FP64 on the CUDA cores and rounded once (an FP32-accurate factor carries
+                             about cond(H) u32 of relative error into H^{-1}; GB300 has no FP64
+                             tensor path at useful rates). */
     void *stream;         /* cudaStream_t, or NULL for a library-created stream */
 } qp_opts;
 
@@ -144,6 +163,8 @@ typedef struct {
     int op64_switch_iter; /* QP_PREC_FP32: IPM iteration of the switch to the FP64 operator, or -1 */
     int pc64_switch_iter; /* QP_PREC_FP32: IPM iteration of the switch to an FP64 P_H factor, or -1 */
     int pc_switch_iter;   /* QP_PC_AUTO: IPM iteration of the switch from P_L to P_H, or -1 */
+    int factor_tc;        /* 1 if the FP32 K0 factor was formed on the tensor cores (qp_opts.factor_tc) */
+    int pcg_form_used;    /* the handle's pcg_form (QP_FORM_AUTO resolved at qp_create) */
 } qp_stats;
 
 /* Fill *opts with the defaults listed in the struct comments. */

@@ -19,6 +19,7 @@ QP_EMAXIT, QP_ENUMERIC, QP_ETIMEOUT, QP_EAGAIN, QP_ECUDA, QP_ESTATE = -5, -6, -7
 QP_PREC_FP64, QP_PREC_FP32 = 0, 1
 QP_PC_AUTO, QP_PC_PL, QP_PC_PH_EXACT, QP_PC_PH_DIAG, QP_PC_NONE = 0, 1, 2, 3, 4
 QP_MODE_PARITY, QP_MODE_PAPER = 0, 1
+QP_FORM_AUTO = -1
 QP_PTR_HOST, QP_PTR_DEVICE = 0, 1
 
 EXPORTED = [
@@ -38,7 +39,7 @@ class qp_opts(ct.Structure):
         ("pcg_tol", ct.c_double), ("refine_tol", ct.c_double), ("tol_feas", ct.c_double),
         ("tol_mu", ct.c_double), ("pcg_check_every", ct.c_int), ("mixed_fallback", ct.c_int),
         ("pcg_blocks", ct.c_int), ("blocking_wait", ct.c_int), ("pcg_form", ct.c_int),
-        ("stream", ct.c_void_p),
+        ("factor_tc", ct.c_int), ("stream", ct.c_void_p),
     ]
 
 
@@ -81,7 +82,7 @@ class qp_stats(ct.Structure):
         ("t_factor_ms", ct.c_double), ("t_solve_ms", ct.c_double), ("t_pcg_ms", ct.c_double),
         ("t_precond_ms", ct.c_double), ("op64_solves", ct.c_int), ("op64_switch_iter", ct.c_int),
         ("pc64_switch_iter", ct.c_int),
-        ("pc_switch_iter", ct.c_int),
+        ("pc_switch_iter", ct.c_int), ("factor_tc", ct.c_int), ("pcg_form_used", ct.c_int),
     ]
 
     def as_dict(self):

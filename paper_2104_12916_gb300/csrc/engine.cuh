@@ -228,6 +228,9 @@ public:
 
     Engine(int n_, int m1_, int m2_, const qp_opts& o) {
         n = n_; m1 = m1_; m2 = m2_; opt = o;
+        form_auto = (opt.pcg_form == QP_FORM_AUTO);
+        opt.pcg_form = resolve_form(opt.pcg_form, n, m1);
+        stats.pcg_form_used = opt.pcg_form;
         f64 = (opt.precision == QP_PREC_FP64);
         use64 = f64;
         pc64 = f64;
@@ -286,7 +289,19 @@ public:
     // copies, the C R^{-1} product of T), counted at their padded sizes with the
     // arena's 256-byte slack, for each precision and preconditioner the options
     // allow the solve to reach (FP32 may move to FP64; AUTO may move to P_H).
-    static size_t bytes_bound(int n, int m1, int m2, const qp_opts& o) {
+    // QP_FORM_AUTO: the low-rank form (K_F = D + V V', V = C Z, M0 = Z Z') when the QP
+    // has few degrees of freedom (2 m1 >= n, r = n - m1 between 1 and 1024: V streams
+    // 2 m2 r elements per iteration against 2 m2 n + n^2 for C', M0, C, and Z costs r
+    // steps of a pivoted Cholesky once per QP); otherwise the M0 form.
+    static int resolve_form(int form, int n, int m1) {
+        if (form != QP_FORM_AUTO) return form;
+        const int r = n - m1;
+        return (2 * m1 >= n && r >= 1 && r <= 1024) ? 3 : 0;
+    }
+
+    static size_t bytes_bound(int n, int m1, int m2, const qp_opts& oin) {
+        qp_opts o = oin;
+        o.pcg_form = resolve_form(o.pcg_form, n, m1);
         auto mat = [](int r, int c, size_t es) {
             return (size_t)std::max(r, 1) * (size_t)pad_ld(std::max(c, 1)) * es + 256;
         };
@@ -541,6 +556,7 @@ public:
     }
 
     bool fp32_pivot_warn = false;
+    bool form_auto = false;   // pcg_form was QP_FORM_AUTO
 
     // Scratch of the tensor-core products (TF32 hi/lo splits of their operands),
     // grown on demand and released with the handle.
@@ -575,20 +591,114 @@ public:
         return std::max(std::max(t, pi), chol_tc_scratch(m2));
     }
 
+    // The FP32 operator's factor formed in FP32 storage with the dense contractions on
+    // the tensor cores (FP32-accurate 3xTF32 splits) and FP64 pivots on the diagonal
+    // blocks: H = R'R with its inverse (blocked, the trailing and inverse updates on
+    // tcgen05), G = A R^{-1}, S = G G', L_S and its inverse, Gt = L_S^{-1} G,
+    // Et = Gt R^{-T}, and M0 = R^{-1}R^{-T} - Et'Et.  Returns false (nothing kept) if a
+    // pivot falls below FP32 resolution (1e-6 of its original diagonal entry) or a
+    // tensor map cannot be made; the caller then rounds the FP64 factor instead.
+    bool factor_tc32() {
+        Op<float>& o = o32;
+        const long long ldn = pad_ld(n), ldm = pad_ld(std::max(m1, 1));
+        const double rel = 1e-6;
+        chol_inv_prepare<float, double>();
+        float *Hw = nullptr, *Aw = nullptr, *G = nullptr, *GT = nullptr, *S = nullptr;
+        auto galloc = [&](float** p, size_t count) {
+            if (cudaMallocAsync(p, count * sizeof(float) + 256, s) != cudaSuccess) { cudaGetLastError(); throw NoMem{}; }
+            PCG_CK(cudaMemsetAsync(*p, 0, count * sizeof(float) + 256, s));
+        };
+        // scratch: hi/lo splits of two operands of up to n x ldn, and the blocked Cholesky
+        float* sc = tc_scratch(std::max<size_t>(4 * (size_t)n * (size_t)ldn, chol_tc_scratch(n)));
+        float *ah = sc, *al = ah + (size_t)n * ldn, *bh = al + (size_t)n * ldn, *bl = bh + (size_t)n * ldn;
+        bool ok = true;
+        auto split = [&](const float* x, long long ldx, int rows, int cols, float* hi, float* lo) {
+            tc_split(x, ldx, rows, cols, hi, lo, ldx, s);
+        };
+        // C = alpha X Y' + beta C with X (M x K), Y (N x K) K-major, both split first
+        auto tcmm = [&](int M, int N, int K, float alpha, const float* X, long long ldx, const float* Y, long long ldy,
+                        float beta, float* Cm, long long ldc, bool lower) {
+            if (!ok || M <= 0 || N <= 0) return;
+            split(X, ldx, M, K, ah, al);
+            split(Y, ldy, N, K, bh, bl);
+            ok = tc_gemm(M, N, K, alpha, ah, al, ldx, bh, bl, ldy, beta, Cm, ldc, true, lower, d_tcerr, s);
+            if (!ok) cudaGetLastError();
+        };
+        PCG_CK(cudaMemsetAsync(d_tcerr, 0, sizeof(int), s));
+        PCG_CK(cudaMemsetAsync(d_info, 0, 8 * sizeof(int), s));
+        galloc(&Hw, (size_t)n * ldn);
+        PCG_CK(cudaMemsetAsync(o.WH.p, 0, (size_t)n * o.WH.ld * sizeof(float), s));
+        convert2d<double, float>(H.p, H.ld, Hw, ldn, n, n, s);
+        chol_inv_tc<double>(Hw, ldn, o.WH.p, o.WH.ld, n, 0, rel, d_info, s, tc_scratch(0), d_tcerr, diag0);
+        transpose<float>(o.WH.p, o.WH.ld, o.WHT.p, o.WHT.ld, n, n, s);
+        if (m1) {
+            galloc(&Aw, (size_t)m1 * ldn);
+            galloc(&G, (size_t)m1 * ldn);
+            galloc(&GT, (size_t)n * ldm);
+            galloc(&S, (size_t)m1 * ldm);
+            PCG_CK(cudaMemsetAsync(o.WS.p, 0, (size_t)m1 * o.WS.ld * sizeof(float), s));
+            convert2d<double, float>(A.p, A.ld, Aw, ldn, m1, n, s);
+            tcmm(m1, n, n, 1.0f, Aw, ldn, o.WH.p, o.WH.ld, 0.0f, G, ldn, false);        // G = A R^{-1} = A WH'
+            tcmm(m1, m1, n, 1.0f, G, ldn, G, ldn, 0.0f, S, ldm, true);                  // S = G G' (lower)
+            if (ok) chol_inv_tc<double>(S, ldm, o.WS.p, o.WS.ld, m1, 0, rel, d_info + 2, s, tc_scratch(0), d_tcerr, diag0);
+            transpose<float>(G, ldn, GT, ldm, m1, n, s);
+            tcmm(m1, n, m1, 1.0f, o.WS.p, o.WS.ld, GT, ldm, 0.0f, o.Gt.p, o.Gt.ld, false);   // Gt = L_S^{-1} G
+            transpose<float>(o.Gt.p, o.Gt.ld, o.GtT.p, o.GtT.ld, m1, n, s);
+            transpose<float>(o.WS.p, o.WS.ld, o.WST.p, o.WST.ld, m1, m1, s);
+            tcmm(m1, n, n, 1.0f, o.Gt.p, o.Gt.ld, o.WHT.p, o.WHT.ld, 0.0f, o.Et.p, o.Et.ld, false);   // Et = Gt WH
+            transpose<float>(o.Et.p, o.Et.ld, o.EtT.p, o.EtT.ld, m1, n, s);
+        }
+        if (o.M0.p) {
+            tcmm(n, n, n, 1.0f, o.WHT.p, o.WHT.ld, o.WHT.p, o.WHT.ld, 0.0f, o.M0.p, o.M0.ld, false);   // R^{-1}R^{-T}
+            if (m1) tcmm(n, n, m1, -1.0f, o.EtT.p, o.EtT.ld, o.EtT.p, o.EtT.ld, 1.0f, o.M0.p, o.M0.ld, false);
+        }
+        convert2d<double, float>(C.p, C.ld, o.CW.p, o.CW.ld, m2, n, s);
+        convert2d<double, float>(CT.p, CT.ld, o.CWT.p, o.CWT.ld, n, m2, s);
+        if (crp && !o.cval) {
+            float* v = arena.alloc<float>((size_t)std::max(nnz, 1LL));
+            float* vt = arena.alloc<float>((size_t)std::max(nnz, 1LL));
+            convert1d<double, float>((int)nnz, cval64, 1.0, v, s);
+            convert1d<double, float>((int)nnz, ctval64, 1.0, vt, s);
+            o.cval = v;
+            o.ctval = vt;
+        }
+        PCG_CK(cudaMemcpyAsync(h_info, d_info, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        cudaFreeAsync(Hw, s);
+        if (Aw) cudaFreeAsync(Aw, s);
+        if (G) cudaFreeAsync(G, s);
+        if (GT) cudaFreeAsync(GT, s);
+        if (S) cudaFreeAsync(S, s);
+        wait_stream();
+        PCG_CK(cudaGetLastError());
+        tc_check();
+        if (!ok || h_info[0] != 0 || h_info[2] != 0) {
+            if (verbose) std::fprintf(stderr, "  tensor-core FP32 factor declined (tc %d, pivots %d %d): FP64 factor\n",
+                                      (int)ok, h_info[0], h_info[2]);
+            return false;
+        }
+        stats.factor_tc = 1;
+        return true;
+    }
+
     template <typename TO>
     void factor_op() {
         Op<TO>& o = op<TO>();
         if (o.factored) return;
         constexpr bool is64 = std::is_same<TO, double>::value;
         if constexpr (!is64) {
-            // FP32 operator: the FP64 factor rounded once (an FP32 factorization would
-            // add about cond(R) u32 to every entry; rounding adds u32 of the entry)
-            factor_op<double>();
             if (!o.px) {
                 alloc_op_vectors(o);
                 o.CW.alloc(arena, m2, n);
                 o.CWT.alloc(arena, n, m2);
             }
+            // qp_opts.factor_tc: the FP32 factor itself on the tensor cores (forms 0 and 2)
+            if (opt.factor_tc && (opt.pcg_form == 0 || opt.pcg_form == 2) && factor_tc32()) {
+                o.factored = true;
+                return;
+            }
+            // FP32 operator: the FP64 factor rounded once (an FP32 factorization would
+            // add about cond(R) u32 to every entry; rounding adds u32 of the entry)
+            factor_op<double>();
             convert2d<double, TO>(C.p, C.ld, o.CW.p, o.CW.ld, m2, n, s);
             convert2d<double, TO>(CT.p, CT.ld, o.CWT.p, o.CWT.ld, n, m2, s);
             auto rnd = [&](const Mat<double>& a, Mat<TO>& b) {
@@ -739,7 +849,9 @@ public:
             wait_stream();
             if (h_info[5] != r) {
                 if (verbose) std::fprintf(stderr, "  low-rank form: M0 has rank %d, expected %d\n", h_info[5], r);
-                throw QpError{QP_ESINGULAR};
+                if (!form_auto) throw QpError{QP_ESINGULAR};
+                opt.pcg_form = 0;            // chosen by QP_FORM_AUTO: the M0 form (M0 is held)
+                stats.pcg_form_used = 0;
             }
         }
         if (opt.pcg_form == 1) {
@@ -805,6 +917,11 @@ public:
     // The persistent kernel applies an FP32 P_H factor as one symmetric product
     // P~^{-1} = W'W (formed each IPM iteration, m2^3 flops at FP32 rates) and an FP64
     // one as its two triangles W, then W' (one more phase, no FP64 product).
+    // The FP32 Cholesky, its inverse and W'W run on the CUDA cores (round to
+    // nearest): the tensor cores' FP32 accumulation is biased toward zero, and
+    // W'W formed there (K = m2 terms) was indefinite enough in P~'s small
+    // eigendirections that PCG stopped converging (5,600 instead of 200 PCG
+    // iterations per Newton direction on the n=2000 workload).
     template <typename TP>
     static constexpr bool ph_one_phase() { return std::is_same<TP, float>::value; }
 
@@ -901,33 +1018,14 @@ public:
             build_scaled_ph_kernel<TP><<<304 * 4, 256, 0, s>>>(P.Tm.p, P.Tm.ld, P.Dp, P.Pm.p, P.Pm.ld, P.sg, m2, shift);
             PCG_CK(cudaMemsetAsync(P.WPl.p, 0, (size_t)m2 * P.WPl.ld * sizeof(TP), s));
             PCG_CK(cudaMemsetAsync(d_info + 4, 0, sizeof(int), s));
-            if constexpr (std::is_same<TP, float>::value) {
-                PCG_CK(cudaMemsetAsync(d_tcerr, 0, sizeof(int), s));
-                chol_inv_tc<float>(P.Pm.p, P.Pm.ld, P.WPl.p, P.WPl.ld, m2, 1, floor, d_info + 4, s,
-                                   tc_scratch(tc_scratch_floats(n, m2)), d_tcerr);
-            } else {
-                chol_inv<TP, TP>(P.Pm.p, P.Pm.ld, P.WPl.p, P.WPl.ld, m2, 1, floor, d_info + 4, s);
-            }
+            chol_inv<TP, TP>(P.Pm.p, P.Pm.ld, P.WPl.p, P.WPl.ld, m2, 1, floor, d_info + 4, s);
             PCG_CK(cudaMemcpyAsync(h_info + 4, d_info + 4, sizeof(int), cudaMemcpyDeviceToHost, s));
             sync_check();
             if (h_info[4] == 0) break;
             shift = (shift == 0.0) ? (is64 ? 1e-10 : 1e-4) : shift * 10.0;
         }
         transpose<TP>(P.WPl.p, P.WPl.ld, P.WPu.p, P.WPu.ld, m2, m2, s);
-        bool pi_tc = false;
-        if constexpr (std::is_same<TP, float>::value) {
-            if (P.PI.p) {
-                // P~^{-1} = W'W = U U' with U = W' (upper, stored as WPu): tensor cores
-                const long long ldm = pad_ld(m2);
-                float* sc = tc_scratch(tc_scratch_floats(n, m2));
-                float *uh = sc, *ul = sc + (size_t)m2 * ldm;
-                tc_split(P.WPu.p, P.WPu.ld, m2, m2, uh, ul, ldm, s);
-                pi_tc = tc_gemm(m2, m2, m2, 1.0f, uh, ul, ldm, uh, ul, ldm, 0.0f, P.PI.p, P.PI.ld, true, false,
-                                d_tcerr, s);
-                if (!pi_tc) cudaGetLastError();
-            }
-        }
-        if (P.PI.p && !pi_tc) {
+        if (P.PI.p) {
             // P~^{-1} = W' W (W = L^{-1} lower): opA(i,k) = W[k,i], zero for k < i;
             // opB(k,j) = W[k,j], zero for k < j
             GemmArgs<TP> g{};
@@ -937,7 +1035,6 @@ public:
             g.C = P.PI.p; g.ldc = P.PI.ld; g.alpha = TP(1); g.beta = TP(0);
             gemm<TP>(g, s);
         }
-        if (std::is_same<TP, float>::value) tc_check();
         P.shift = shift;
         if (verbose && shift > 0) std::fprintf(stderr, "  P_H shift %.1e\n", shift);
         return shift;

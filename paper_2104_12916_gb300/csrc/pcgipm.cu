@@ -80,7 +80,8 @@ void qp_opts_default(qp_opts* o) {
     o->mixed_fallback = 1;
     o->pcg_blocks = 0;
     o->blocking_wait = 0;
-    o->pcg_form = 0;
+    o->pcg_form = QP_FORM_AUTO;
+    o->factor_tc = 0;
     o->stream = nullptr;
 }
 
@@ -97,7 +98,7 @@ static int create_common(qp_t* out, int n, int m1, int m2, const double* H, cons
     if (opts) o = *opts;
     if (o.precision != QP_PREC_FP32 && o.precision != QP_PREC_FP64) return QP_EINVAL;
     if (o.precond < QP_PC_AUTO || o.precond > QP_PC_NONE) return QP_EINVAL;
-    if (o.pcg_form < 0 || o.pcg_form > 3) return QP_EINVAL;
+    if (o.pcg_form < QP_FORM_AUTO || o.pcg_form > 3) return QP_EINVAL;
     return guarded([&]() {
         std::unique_ptr<qp_s> h(new qp_s);
         h->eng.reset(new Engine(n, m1, m2, o));

@@ -17,11 +17,17 @@
 // slices of A and B into a ring of shared-memory stages with TMA
 // (cp.async.bulk.tensor, 128-byte swizzle, zero fill outside the matrices); one
 // thread of the MMA warp issues tcgen05.mma (kind::tf32, M = 128, N = 128, K = 8
-// per instruction) into an FP32 accumulator in tensor memory and releases each
-// stage with tcgen05.commit; four epilogue warps read the accumulator back with
-// tcgen05.ld (each warp its 32-lane quarter: one row of C per thread) and apply
-// alpha, beta and the bounds.  With `lower_out` only tiles on or below the
-// diagonal run and only elements j <= i are written.
+// per instruction) into FP32 accumulators in tensor memory and releases each
+// stage with tcgen05.commit.  K slice kt goes to accumulator kt mod kTcAcc, so
+// each accumulator sums a quarter of the products: the tensor core's FP32
+// accumulation does not round to nearest, and its error grows with the number
+// of terms summed in one accumulator (one accumulator over K = 4000 made the
+// explicit P~^{-1} = W'W indefinite enough to stall PCG).  Four epilogue warps
+// read the accumulators back with tcgen05.ld (each warp its 32-lane quarter: one
+// row of C per thread), add them in a fixed order, apply alpha, and pass each
+// 32 x 32 piece through shared memory so that every store (and the beta read)
+// covers a row segment of 32 consecutive elements.  With `lower_out` only tiles
+// on or below the diagonal run and only elements j <= i are written.
 //
 // Every wait is bounded (kTcWaitNs of %globaltimer): a wait that gives up sets
 // *err, the kernel skips the remaining work, waits (bounded) for its issued
@@ -42,6 +48,7 @@ constexpr int kTcBM = 128, kTcBN = 128, kTcBK = 32;        // tile; BK = one 128
 constexpr int kTcThreads = 192;                            // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
 constexpr unsigned long long kTcWaitNs = 2000000000ull;     // 2 s bound on any wait
 constexpr int kTcTileBytes = kTcBM * kTcBK * 4;            // 16 KB per operand slice
+constexpr int kTcAcc = 4;                                  // accumulators (128 TMEM columns each)
 
 __device__ __forceinline__ unsigned long long tc_gtimer() {
     unsigned long long t;
@@ -161,9 +168,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         s_fail = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 1) {   // tensor memory: 128 lanes x 128 FP32 columns (the accumulator)
+    if (warp == 1) {   // tensor memory: 128 lanes x kTcAcc * 128 FP32 columns (the accumulators)
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc_smem(&tmem_base)),
-                     "r"(128)
+                     "r"(kTcAcc * kTcBN)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -218,15 +225,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 unsigned char* st = base + (size_t)s * stage_bytes;
                 const uint64_t ah = tc_desc_sw128(st), bh = tc_desc_sw128(st + kTcTileBytes);
                 const uint64_t al = tc_desc_sw128(st + 2 * kTcTileBytes), bl = tc_desc_sw128(st + 3 * kTcTileBytes);
+                const uint32_t d = tmem + (uint32_t)((kt % kTcAcc) * kTcBN);
 #pragma unroll
                 for (int kk = 0; kk < kTcBK / 8; ++kk) {
                     // K = 8 TF32 = 32 bytes per instruction: advance the start address by 2 (x 16 B)
                     const uint64_t o = (uint64_t)(kk * 2);
-                    const int acc = (kt > 0 || kk > 0) ? 1 : 0;
-                    tc_mma_tf32(tmem, ah + o, bh + o, idesc, acc);
+                    const int acc = (kt >= kTcAcc || kk > 0) ? 1 : 0;
+                    tc_mma_tf32(d, ah + o, bh + o, idesc, acc);
                     if (p.split) {
-                        tc_mma_tf32(tmem, ah + o, bl + o, idesc, 1);
-                        tc_mma_tf32(tmem, al + o, bh + o, idesc, 1);
+                        tc_mma_tf32(d, ah + o, bl + o, idesc, 1);
+                        tc_mma_tf32(d, al + o, bh + o, idesc, 1);
                     }
                 }
                 tc_commit(&empty[s]);   // the stage is free once these MMAs have read it
@@ -236,36 +244,53 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     } else {
         // ---- epilogue: warps 2..5, TMEM lane quarter (warp % 4), one row per thread
         const int q = warp & 3;
-        const int row = tm * kTcBM + q * 32 + lane;
         const bool ok = tc_mbar_wait(&accum, 0u);
         if (!ok) atomicExch(p.err, 1);
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const bool write = ok && ktiles > 0 && !*(volatile int*)&s_fail;
+        // every MMA has completed (or none will run): the stages are free for the
+        // 32 x 33 staging piece of each epilogue warp
+        const bool write = __all_sync(0xffffffffu, ok && ktiles > 0 && !*(volatile int*)&s_fail);
+        float* stg = reinterpret_cast<float*>(base) + q * 32 * 33;
+        const int nacc = ktiles < kTcAcc ? ktiles : kTcAcc;
+        const int row0 = tm * kTcBM + q * 32;
 #pragma unroll 1
         for (int c0 = 0; c0 < kTcBN; c0 += 32) {
-            uint32_t v[32];
-            const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0;
-            asm volatile(
-                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-                  "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
-                  "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
-                  "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-                : "r"(taddr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (write && row < p.M) {
-                float* crow = p.C + (long long)row * p.ldc;
+            float acc[32];
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int col = tn * kTcBN + c0 + j;
-                    if (col < p.N && (!p.lower_out || col <= row)) {
-                        float r = p.alpha * __uint_as_float(v[j]);
-                        if (p.beta != 0.0f) r = fmaf(p.beta, crow[col], r);
-                        crow[col] = r;
+            for (int j = 0; j < 32; ++j) acc[j] = 0.0f;
+#pragma unroll 1
+            for (int a = 0; a < nacc; ++a) {   // (nacc is the same in every lane)
+                uint32_t v[32];
+                const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(a * kTcBN + c0);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                      "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                      "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+                      "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                    : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int j = 0; j < 32; ++j) acc[j] += __uint_as_float(v[j]);
+            }
+            if (write) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j) stg[lane * 33 + j] = p.alpha * acc[j];
+                __syncwarp();
+                const int col = tn * kTcBN + c0 + lane;
+#pragma unroll 4
+                for (int r = 0; r < 32; ++r) {
+                    const int row = row0 + r;
+                    if (row < p.M && col < p.N && (!p.lower_out || col <= row)) {
+                        float* cp = p.C + (long long)row * p.ldc + col;
+                        float x = stg[r * 33 + lane];
+                        if (p.beta != 0.0f) x = fmaf(p.beta, *cp, x);
+                        *cp = x;
                     }
                 }
+                __syncwarp();
             }
         }
     }
@@ -273,7 +298,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     __syncthreads();
     if (warp == 1) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcAcc * kTcBN)
+                     : "memory");
     }
 }
 

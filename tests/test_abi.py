@@ -45,7 +45,8 @@ def test_host_only_calls(lib):
 
 def test_new_option_defaults(lib):
     o = binding.qp_opts_default()
-    assert o.pcg_blocks == 0 and o.blocking_wait == 0 and o.pcg_form == 0 and o.mixed_fallback == 1
+    assert o.pcg_blocks == 0 and o.blocking_wait == 0 and o.mixed_fallback == 1
+    assert o.pcg_form == binding.QP_FORM_AUTO and o.factor_tc == 0
     assert o.precond == binding.QP_PC_AUTO and o.pcg_mode == binding.QP_MODE_PARITY
 
 
@@ -90,3 +91,15 @@ def test_device_calls_fail_cleanly_without_a_gpu(lib):
     with pytest.raises(binding.QPError) as e:
         binding.Server(budget_bytes=1 << 30, max_slots=2)
     assert e.value.status == binding.QP_ECUDA
+
+
+def test_auto_form_resolution(lib):
+    """QP_FORM_AUTO (host logic): the low-rank form for few degrees of freedom
+    (2 m1 >= n, 1 <= n - m1 <= 1024), the M0 form otherwise -- seen through the
+    admission bound, which sizes the form the handle will hold."""
+    for n, m1, m2, want in ((3000, 2600, 6000, 3), (2000, 200, 4000, 0), (400, 200, 900, 3),
+                            (400, 400, 900, 0), (3000, 1500, 4000, 0), (100, 49, 300, 0)):
+        auto = _bound(n, m1, m2, pcg_form=binding.QP_FORM_AUTO)
+        assert auto == _bound(n, m1, m2, pcg_form=want), (n, m1, m2)
+    assert _bound(100, 60, 300, pcg_form=3) != _bound(100, 60, 300, pcg_form=0)
+    assert binding.qp_device_bytes_bound(10, 5, 20, None) > 0

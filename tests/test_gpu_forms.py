@@ -83,3 +83,37 @@ def test_form_ipm_syqp_and_batch_member(B, prec, form):
         assert abs(f - ref.f) / max(abs(ref.f), 1.0) <= 1e-6, q.name
         assert abs(its - ref.iters) <= 2, q.name
         h.close()
+
+
+@pytest.mark.parametrize("form", [0, 2])
+def test_factor_tc_reduced_solve_and_ipm(B, form):
+    """qp_opts.factor_tc: the FP32 K0 factor (and M0) formed on the tcgen05 tensor
+    cores with FP64 pivots on the diagonal blocks.  The reduced solve meets the
+    FP32 bar against the explicit K_F, and a whole IPM solve meets the oracle's
+    (objective 1e-6, iterations within 2, residuals 1e-8) through the FP64
+    refinement; the handle reports that the tensor-core factor was used."""
+    q = qpgen.dense_qp(300, 40, 1100, seed=41)
+    D, rhs = qpgen.pcg_inputs(q.m2, 6, 0.1, 10.0)
+    o = _opts(B, 1, 2, form=form)
+    o.factor_tc = 1
+    h = B.QP.from_qpgen(q, o).factor()
+    assert B.qp_get_stats(h.h)["factor_tc"] == 1
+    dnu = np.zeros(q.m2)
+    st, it, rel = B.qp_pcg_reduced_solve(h.h, D, rhs, dnu, precond=2, tol=1e-5, maxit=20000)
+    K = reduced.kf_explicit(q.H, q.A, q.C, D)
+    ref = np.linalg.solve(K, rhs)
+    assert np.linalg.norm(dnu - ref) / np.linalg.norm(ref) <= 2e-3
+    h.close()
+    q = qpgen.config_qp(0)
+    with open(os.path.join(HERE, "golden", "oracle_config0.json")) as fh:
+        gold = json.load(fh)
+    o = _opts(B, 1, 0, form=form)
+    o.factor_tc = 1
+    h = B.QP.from_qpgen(q, o)
+    st, f, its, _ = B.qp_ipm_solve(h.h)
+    s = B.qp_get_stats(h.h)
+    assert st == B.QP_OK and s["factor_tc"] == 1
+    assert abs(f - gold["f"]) / max(abs(gold["f"]), 1.0) <= 1e-6
+    assert abs(its - gold["ipm_iters"]) <= 2
+    assert s["res_p"] <= 1e-8 and s["res_d"] <= 1e-8
+    h.close()
