@@ -46,7 +46,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--fp64-steps", type=int, default=3, help="timed steps of the FP64 comparison line (at least 3)")
+    ap.add_argument("--fp64-steps", type=int, default=3,
+                    help="timed steps of the FP64 comparison line (at least 3; 0 leaves the line out)")
     ap.add_argument("--config", type=int, default=HEADLINE, choices=[1, 2], help="workload of value (1 or 2)")
     ap.add_argument("--no-extras", action="store_true", help="skip the other workload, batch and serving keys")
     ap.add_argument("--extra-batch", type=int, default=64, help="QPs of the batch key")
@@ -285,10 +286,12 @@ def run_ours(args):
 
     with ClockSampler(local) as clk:
         res, total_ms, ok, launches, solved = timed(main, B.QP_PREC_FP32, args.steps, args.warmup)
-    fp64_steps = max(3, args.fp64_steps)
-    res64, total64, ok64, _, solved64 = timed(main, B.QP_PREC_FP64, fp64_steps, 1)
     value = solved / (total_ms / 1e3)
-    value64 = solved64 / (total64 / 1e3)
+    fp64_steps = max(3, args.fp64_steps) if args.fp64_steps > 0 else 0
+    res64, total64, ok64, value64 = [], 0.0, [], 0.0
+    if fp64_steps:
+        res64, total64, ok64, _, solved64 = timed(main, B.QP_PREC_FP64, fp64_steps, 1)
+        value64 = solved64 / (total64 / 1e3)
     gold = main.gold
 
     peaks = {}
@@ -397,7 +400,8 @@ def run_ours(args):
             "fp64": {"value": round(value64, 4), "unit": "QPs/s", "steps": fp64_steps,
                      "ms_per_step": round(total64 / fp64_steps, 2), "dtype": "f64",
                      "solved": f"{sum(ok64)}/{len(ok64)}", "ipm_iters": [r["ipm"] for r in res64],
-                     "pcg_iters": [r["pcg"] for r in res64], "per_solve": per_solve(res64[-1]) if res64 else None},
+                     "pcg_iters": [r["pcg"] for r in res64],
+                     "per_solve": per_solve(res64[-1]) if res64 else None} if fp64_steps else None,
             "mixed_over_fp64": round(value / value64, 3) if value64 > 0 else None,
             "roofline": roofline, "pcg_iteration": pcg_it, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(launches), "clocks": clk.summary(),

@@ -132,9 +132,10 @@ typedef struct {
                              QP_ESINGULAR if M0's numerical rank is below r; a handle that chose
                              it by QP_FORM_AUTO takes form 0 instead).  All four are the
                              same operator; the per-phase kernels (pcg_check_every < 0) always use
-                             the two triangular solves.  QP_FORM_AUTO (default): 3 when 2 m1 >= n
-                             and 1 <= n - m1 <= 1024 (few degrees of freedom), else 0; the choice
-                             is reported in qp_stats.pcg_form_used. */
+                             the two triangular solves.  QP_FORM_AUTO (default): 3 when C is dense,
+                             1 <= r = n - m1 <= 1024 and 2 m2 r <= (2 m2 n + n^2) / 2 (few degrees
+                             of freedom), else 0; the choice is reported in
+                             qp_stats.pcg_form_used. */
     int factor_tc;        /* QP_PREC_FP32 with pcg_form 0 or 2: 1 forms the FP32 operator's K0 factor
                              (and M0) in FP32 storage with FP64 diagonal-block pivots and the dense
                              contractions -- the blocked Cholesky's trailing and inverse updates,

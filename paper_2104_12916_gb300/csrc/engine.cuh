@@ -226,10 +226,10 @@ public:
         if constexpr (std::is_same<TP, float>::value) return p32; else return p64;
     }
 
-    Engine(int n_, int m1_, int m2_, const qp_opts& o) {
+    Engine(int n_, int m1_, int m2_, const qp_opts& o, bool csr_c = false) {
         n = n_; m1 = m1_; m2 = m2_; opt = o;
         form_auto = (opt.pcg_form == QP_FORM_AUTO);
-        opt.pcg_form = resolve_form(opt.pcg_form, n, m1);
+        opt.pcg_form = resolve_form(opt.pcg_form, n, m1, m2, csr_c);
         stats.pcg_form_used = opt.pcg_form;
         f64 = (opt.precision == QP_PREC_FP64);
         use64 = f64;
@@ -289,19 +289,21 @@ public:
     // copies, the C R^{-1} product of T), counted at their padded sizes with the
     // arena's 256-byte slack, for each precision and preconditioner the options
     // allow the solve to reach (FP32 may move to FP64; AUTO may move to P_H).
-    // QP_FORM_AUTO: the low-rank form (K_F = D + V V', V = C Z, M0 = Z Z') when the QP
-    // has few degrees of freedom (2 m1 >= n, r = n - m1 between 1 and 1024: V streams
-    // 2 m2 r elements per iteration against 2 m2 n + n^2 for C', M0, C, and Z costs r
-    // steps of a pivoted Cholesky once per QP); otherwise the M0 form.
-    static int resolve_form(int form, int n, int m1) {
+    // QP_FORM_AUTO with a dense C: the low-rank form (K_F = D + V V', V = C Z,
+    // M0 = Z Z') when V streams at most half the elements of C', M0 and C
+    // (2 m2 r <= (2 m2 n + n^2) / 2, r = n - m1) and r <= 1024 (Z costs r steps of a
+    // pivoted Cholesky, one grid barrier each, once per QP); otherwise the M0 form.
+    // With C in CSR the M0 form (its C products are sparse row sums; V would be dense).
+    static int resolve_form(int form, int n, int m1, int m2, bool csr) {
         if (form != QP_FORM_AUTO) return form;
-        const int r = n - m1;
-        return (2 * m1 >= n && r >= 1 && r <= 1024) ? 3 : 0;
+        const double r = n - m1;
+        const double lowrank = 2.0 * m2 * r, m0form = 2.0 * m2 * n + (double)n * n;
+        return (!csr && r >= 1 && r <= 1024 && lowrank <= 0.5 * m0form) ? 3 : 0;
     }
 
     static size_t bytes_bound(int n, int m1, int m2, const qp_opts& oin) {
         qp_opts o = oin;
-        o.pcg_form = resolve_form(o.pcg_form, n, m1);
+        o.pcg_form = resolve_form(o.pcg_form, n, m1, m2, false);   // (a CSR handle never holds more)
         auto mat = [](int r, int c, size_t es) {
             return (size_t)std::max(r, 1) * (size_t)pad_ld(std::max(c, 1)) * es + 256;
         };
@@ -1550,15 +1552,17 @@ public:
 
     bool use_fused() const { return opt.pcg_check_every >= 0; }
 
-    // CTAs of the persistent kernel: about one per 512 KB streamed per iteration,
-    // up to one per SM; a QP of at most 32 such units gets between 8 and
-    // kMaxClusterBlocks (one cluster), so that the kernels of several QPs solved
-    // concurrently share the GPU.
+    // CTAs of the persistent kernel.  A QP streaming at most 32 x 512 KB per iteration
+    // gets between 8 and kMaxClusterBlocks (one cluster, about one per 512 KB), so
+    // that the kernels of several QPs solved concurrently share the GPU; a larger
+    // one about one CTA per 128 KB, up to one per SM (a block's chunks of one
+    // iteration then fit its ring, and an operator that stays in L2 -- the
+    // low-rank form of the n=3000 few-dof workload, 19.6 MB -- is read by every SM).
     int fused_grid(int sms) const {
         const double by = bytes_per_iter(resolve_pc(opt.precond, n, m1));
         const int want = (int)std::ceil(by / (512.0 * 1024.0));
         int g = (want <= 2 * kMaxClusterBlocks) ? std::min(sms, std::max(8, std::min(want, kMaxClusterBlocks)))
-                                                : std::min(sms, want);
+                                                : std::min(sms, (int)std::ceil(by / (128.0 * 1024.0)));
         if (opt.pcg_blocks > 0) g = std::min(g, opt.pcg_blocks);
         return g;
     }

@@ -101,7 +101,7 @@ static int create_common(qp_t* out, int n, int m1, int m2, const double* H, cons
     if (o.pcg_form < QP_FORM_AUTO || o.pcg_form > 3) return QP_EINVAL;
     return guarded([&]() {
         std::unique_ptr<qp_s> h(new qp_s);
-        h->eng.reset(new Engine(n, m1, m2, o));
+        h->eng.reset(new Engine(n, m1, m2, o, csr != nullptr));
         h->eng->load(H, c, A, b, C, d, ptr_kind, csr);
         *out = h.release();
         return QP_OK;

@@ -94,11 +94,13 @@ def test_device_calls_fail_cleanly_without_a_gpu(lib):
 
 
 def test_auto_form_resolution(lib):
-    """QP_FORM_AUTO (host logic): the low-rank form for few degrees of freedom
-    (2 m1 >= n, 1 <= n - m1 <= 1024), the M0 form otherwise -- seen through the
-    admission bound, which sizes the form the handle will hold."""
+    """QP_FORM_AUTO (host logic): the low-rank form when V = C Z streams at most
+    half of what C', M0 and C stream (2 m2 r <= (2 m2 n + n^2) / 2, r = n - m1 in
+    [1, 1024]), the M0 form otherwise -- seen through the admission bound, which
+    sizes the form the handle will hold."""
     for n, m1, m2, want in ((3000, 2600, 6000, 3), (2000, 200, 4000, 0), (400, 200, 900, 3),
-                            (400, 400, 900, 0), (3000, 1500, 4000, 0), (100, 49, 300, 0)):
+                            (400, 400, 900, 0), (3000, 1500, 4000, 0), (100, 40, 300, 0),
+                            (100, 50, 300, 3), (1000, 300, 2000, 0)):
         auto = _bound(n, m1, m2, pcg_form=binding.QP_FORM_AUTO)
         assert auto == _bound(n, m1, m2, pcg_form=want), (n, m1, m2)
     assert _bound(100, 60, 300, pcg_form=3) != _bound(100, 60, 300, pcg_form=0)
