@@ -1330,10 +1330,10 @@ public:
     }
 
     // Ring depth: as deep as the block's shared-memory limit allows after the staged
-    // vector, the three m2-vector caches and the per-row partials (at most kMaxSlots).
+    // vector, the m2-vector caches and the per-row partials (at most kMaxSlots).
     template <typename TO, typename TP>
-    int fused_slots(const FusedPlan& F, int slot_bytes) const {
-        const size_t sp = fused_spart_offset<TO>(fused_xs_bytes<TO, TP>(F), m2);
+    int fused_slots(const FusedPlan& F, int slot_bytes, int qcache) const {
+        const size_t sp = fused_spart_offset<TO>(fused_xs_bytes<TO, TP>(F), m2, qcache);
         const size_t off = fused_ring_offset((sp + F.spart_bytes + 15) / 16 * 16, F.xo_bytes);
         const size_t lim = fused_smem_limit();
         const size_t per = slot_bytes + 2 * sizeof(uint64_t) + sizeof(int);
@@ -1395,17 +1395,19 @@ public:
         }
         auto kern = pcg_fused_kernel<TO, TP, PC, NT>;
         fa.xs_bytes = fused_xs_bytes<TO, TP>(F);
-        fa.spart_off = fused_spart_offset<TO>(fa.xs_bytes, m2);
+        // A QP whose grid covers most of the GPU takes the deepest ring that fits; a
+        // small one (batched with others) a shallow ring, so that the blocks of several
+        // QPs share an SM.  Without room for min_slots(grid) slots beside the q cache
+        // (FP64 with a large m2), the cache gives way to the ring.
+        fa.slot_bytes = slot_bytes_for(grid);
+        fa.qcache = fused_qcache<TO, TP>(F, grid);
+        fa.spart_off = fused_spart_offset<TO>(fa.xs_bytes, m2, fa.qcache);
         fa.xo_off = (fa.spart_off + F.spart_bytes + 15) / 16 * 16;
         fa.ring_off = fused_ring_offset(fa.xo_off, F.xo_bytes);
         int per_sm = 0;
-        // A QP whose grid covers most of the GPU takes the deepest ring that fits; a
-        // small one (batched with others) a shallow ring, so that the blocks of several
-        // QPs share an SM.
-        fa.slot_bytes = slot_bytes_for(grid);
-        fa.slots = fused_slots<TO, TP>(F, fa.slot_bytes);
+        fa.slots = fused_slots<TO, TP>(F, fa.slot_bytes, fa.qcache);
         if (2 * grid < sms) fa.slots = std::min(fa.slots, kSmallRingSlots);
-        if (fa.slots < min_slots(grid)) {
+        if (fa.slots < (fa.qcache == 1 ? min_slots(grid) : kMinSlotsNoCache)) {
             if (verbose) std::fprintf(stderr, "  persistent PCG: %d ring slots of %d bytes do not fit\n", fa.slots, fa.slot_bytes);
             throw QpError{QP_ENOMEM};
         }
@@ -1544,11 +1546,23 @@ public:
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const int grid = fused_grid(sms);
         const FusedPlan F = plan_fused<TO, TP>(kind, grid);
-        return fused_slots<TO, TP>(F, slot_bytes_for(grid)) >= min_slots(grid);
+        return fused_qcache<TO, TP>(F, grid) >= 0;
     }
     // Fewest ring slots the persistent kernel runs with: 16 KB slots stream at the copy
     // rate with a handful in flight; 4 KB slots need one per consumer warp.
     static int min_slots(int grid) { return grid > kMaxClusterBlocks ? 6 : Blk<kSmallBlock>::warps; }
+    // Fewest slots without the q cache (a large-grid ring of three 16 KB slots still
+    // beats the per-phase kernels, whose launches cost more than the shallow ring).
+    static constexpr int kMinSlotsNoCache = 3;
+    // 1: the q cache and min_slots(grid) slots fit; 0: only without the cache (large
+    // grids); -1: neither (the per-phase kernels run instead).
+    template <typename TO, typename TP>
+    int fused_qcache(const FusedPlan& F, int grid) const {
+        const int sb = slot_bytes_for(grid);
+        if (fused_slots<TO, TP>(F, sb, 1) >= min_slots(grid)) return 1;
+        if (grid > kMaxClusterBlocks && fused_slots<TO, TP>(F, sb, 0) >= kMinSlotsNoCache) return 0;
+        return -1;
+    }
 
     bool use_fused() const { return opt.pcg_check_every >= 0; }
 
@@ -1888,9 +1902,9 @@ public:
     // Newton direction for the rhs (fg, fe, fa) already in place; result in (ox, ol, on).
     // PARITY mode refines against the FP64 residual of the 3x3 system.  With the FP32
     // operator a sweep contracts by about max(PCG tolerance, operator error); the next
-    // corrections are then solved only to half that contraction, and a contraction
-    // worse than 1/4 (or a correction that increases the residual) moves the QP to the
-    // FP64 operator.
+    // corrections are then solved only to half that contraction (and never tighter than
+    // a tenth of the reduction still needed), and a contraction worse than 1/4 (or a
+    // correction that increases the residual) moves the QP to the FP64 operator.
     int newton_solve(double* ox, double* ol, double* on) {
         const int kind = pc_kind(ipm_pc);
         const bool paper = (opt.pcg_mode == QP_MODE_PAPER);
@@ -1924,6 +1938,10 @@ public:
             }
             double ctol = base_tol();
             if (!use64 && opt.pcg_tol <= 0) ctol = std::min(1e-1, std::max(ctol, 0.5 * contraction));
+            // A correction only has to take the residual to the refinement target: solve it
+            // to a tenth of the reduction still needed (the last sweep of an FP64 direction
+            // then runs at about 1e-4 instead of 1e-10).
+            if (opt.pcg_tol <= 0) ctol = std::min(1e-1, std::max(ctol, 0.1 * std::sqrt(rtol2 / prev)));
             last = prev;
             it = reduced_solve(rho_g, rho_e, rho_a, tx, tl, tn, kind, ctol, maxit, std::sqrt(prev));
             if (it < 0) return QP_ENUMERIC;

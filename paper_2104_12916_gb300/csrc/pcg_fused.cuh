@@ -57,6 +57,8 @@ template <int NT> struct Blk {
 };
 constexpr int kBigSlotBytes = 16384;              // ring slot of a QP spread over the GPU
 constexpr int kSmallSlotBytes = 4096;             // ring slot of a small QP (its rows are short)
+static_assert((kBigSlotBytes & (kBigSlotBytes - 1)) == 0 && (kSmallSlotBytes & (kSmallSlotBytes - 1)) == 0,
+              "slot sizes are powers of two (chdiv)");
 constexpr int kMaxSlots = 64;                     // two slots per producer lane at most
 constexpr int kSmallRingSlots = 14;               // ring of a QP whose grid covers a small part of the GPU
 constexpr int kMaxClusterBlocks = 16;             // grids up to this size launch as one cluster
@@ -114,24 +116,34 @@ struct Phase {
 // chunk c spans [c CH, (c + 1) CH) (global offsets, so that the segments of a row
 // -- and every sum -- are the same for any grid); a block copies the chunks that
 // meet its rows, clipped to them.
-__host__ __device__ inline int flat_first_chunk(long long r, long long ld, int CH) { return (int)(r * ld / CH); }
+// x / CH for x >= 0: CH, the elements of one ring slot (4 or 16 KB of 4- or 8-byte
+// elements), is a power of two, so the quotient is a shift.
+__host__ __device__ __forceinline__ long long chdiv(long long x, int CH) {
+#ifdef __CUDA_ARCH__
+    return x >> (__ffs(CH) - 1);
+#else
+    return x >> __builtin_ctz((unsigned)CH);
+#endif
+}
+__host__ __device__ inline int flat_first_chunk(long long r, long long ld, int CH) { return (int)chdiv(r * ld, CH); }
 __host__ __device__ inline int flat_row_chunks(long long r, long long ld, int CH) {
-    return (int)(((r + 1) * ld - 1) / CH) - (int)(r * ld / CH) + 1;
+    return (int)chdiv((r + 1) * ld - 1, CH) - (int)chdiv(r * ld, CH) + 1;
 }
 // chunks meeting rows [rb0, rb1)
 __host__ __device__ inline int flat_items(long long rb0, long long rb1, long long ld, int CH) {
     if (rb1 <= rb0) return 0;
-    return (int)((rb1 * ld + CH - 1) / CH) - (int)(rb0 * ld / CH);
+    return (int)chdiv(rb1 * ld + CH - 1, CH) - (int)chdiv(rb0 * ld, CH);
 }
 
 __host__ __device__ inline void part_chunks(const Part& P, int CH, int r, int& c0, int& c1) {
     c0 = c1 = 0;
     if (r < P.r0 || r >= P.r1 || P.rp) return;
-    const int nc = (P.cols + CH - 1) / CH;
+    const int nc = (int)chdiv(P.cols + CH - 1, CH);
     const int i = r - P.r0;
+    const int ic = (int)chdiv(i, CH);
     c1 = nc;
-    if (P.tri == TRI_LOWER) c1 = (i / CH + 1 < nc) ? i / CH + 1 : nc;
-    if (P.tri == TRI_UPPER) c0 = (i / CH < nc) ? i / CH : nc;
+    if (P.tri == TRI_LOWER) c1 = (ic + 1 < nc) ? ic + 1 : nc;
+    if (P.tri == TRI_UPPER) c0 = (ic < nc) ? ic : nc;
 }
 
 __host__ __device__ inline int row_items(const Phase& ph, int CH, int r) {
@@ -385,7 +397,7 @@ __device__ __forceinline__ bool produce_phase(const Phase& ph, const BlockRange 
     const Part& P0 = ph.p[0];
     const TM* fbase = static_cast<const TM*>(P0.M);                   // flat: global element offsets
     const long long fbeg = (long long)br.rb0 * P0.ld, fend = (long long)br.rb1 * P0.ld;
-    const long long fc0 = fbeg / CH;                                    // first chunk meeting the rows
+    const long long fc0 = chdiv(fbeg, CH);                                    // first chunk meeting the rows
     if (i < cnt) {
         me.advance(i, S);
         if (!flat) {
@@ -458,7 +470,7 @@ __device__ __forceinline__ void consume_phase(const Phase& ph, const BlockRange 
         // flat chunks: split each chunk at the row boundaries it crosses
         const long long ld = ph.p[0].ld;
         const long long fbeg = (long long)br.rb0 * ld, fend = (long long)br.rb1 * ld;
-        const long long fc0 = fbeg / CH;
+        const long long fc0 = chdiv(fbeg, CH);
         RingPos me = pos;
         me.advance(i, S);
         while (true) {
@@ -468,35 +480,55 @@ __device__ __forceinline__ void consume_phase(const Phase& ph, const BlockRange 
             const V* sv = reinterpret_cast<const V*>(R.buf + (size_t)slot * R.slot_bytes);
             const long long c = fc0 + i;                         // global chunk
             const long long e0 = max(fbeg, c * CH), e1 = min(fend, (c + 1) * CH);
-            long long rl = e0 / ld;                              // global row
-            TM accs[4];
-            int rows_here = 0;
-            for (long long e = e0; e < e1; ++rl) {
-                const long long se = min(e1, (rl + 1) * ld);
-                const int v0 = (int)((e - e0) / VN), v1 = (int)((se - e0) / VN);
-                // slot vector v holds columns (e0 - rl ld) / VN + v of row rl (exact: both multiples of VN)
-                const int xo = (int)((e0 - rl * ld) / VN);
-                const V* xv = reinterpret_cast<const V*>(xs);
-                TM a0 = TM(0), a1 = TM(0);
-                int v = v0 + lane;
-                for (; v + 32 < v1; v += 64) {
-                    a0 = VT::dot(sv[v], xv[xo + v], a0);
-                    a1 = VT::dot(sv[v + 32], xv[xo + v + 32], a1);
+            // global row (a 32-bit quotient where the offsets allow: 64-bit division is slow)
+            long long rl = (e0 <= 0x7fffffffLL) ? (long long)((unsigned)e0 / (unsigned)ld) : e0 / ld;
+            const V* xv = reinterpret_cast<const V*>(xs);
+            // Row segments four at a time: their dots are independent, and one round of
+            // shuffles reduces all four (a chunk of a short-row matrix holds many rows).
+            // A row that starts inside chunk c has c as its first chunk (k = 0); only the
+            // chunk's first segment may continue a row begun in an earlier chunk.
+            for (long long e = e0; e < e1;) {
+                TM acc[4];
+                long long rg = rl;
+                int nr = 0;
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    acc[t] = TM(0);
+                    if (e < e1) {                                // (the same in every lane)
+                        const long long se = min(e1, (rl + 1) * ld);
+                        const int v0 = (int)((e - e0) / VN), v1 = (int)((se - e0) / VN);
+                        // slot vector v holds columns (e0 - rl ld) / VN + v of row rl (both multiples of VN)
+                        const int xo = (int)((e0 - rl * ld) / VN);
+                        TM a0 = TM(0), a1 = TM(0);
+                        int v = v0 + lane;
+                        for (; v + 32 < v1; v += 64) {
+                            a0 = VT::dot(sv[v], xv[xo + v], a0);
+                            a1 = VT::dot(sv[v + 32], xv[xo + v + 32], a1);
+                        }
+                        if (v < v1) a0 = VT::dot(sv[v], xv[xo + v], a0);
+                        acc[t] = a0 + a1;
+                        e = se;
+                        ++rl;
+                        ++nr;
+                    }
                 }
-                if (v < v1) a0 = VT::dot(sv[v], xv[xo + v], a0);
-                const TM acc = warp_sum(a0 + a1);
-                if (rows_here < 4) accs[rows_here] = acc;
-                else if (lane == 0) spart[(rl - br.rb0) * ph.ncmax + (int)(c - flat_first_chunk(rl, ld, CH))] = acc;
-                ++rows_here;
-                e = se;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
+                }
+                if (lane == 0) {
+                    for (int t = 0; t < nr; ++t) {
+                        const long long r = rg + t;
+                        const int k = (r * ld >= c * CH) ? 0 : (int)(c - flat_first_chunk(r, ld, CH));
+                        spart[(r - br.rb0) * ph.ncmax + k] = acc[t];
+                    }
+                }
             }
             __syncwarp();
             if (lane == 0) {
                 mbar_arrive(&R.empty[slot]);
                 trace_mark(R, 2, me.fill, slot);
-                long long r = e0 / ld;
-                for (int t = 0; t < rows_here && t < 4; ++t, ++r)
-                    spart[(r - br.rb0) * ph.ncmax + (int)(c - flat_first_chunk(r, ld, CH))] = accs[t];
             }
             const int d = (slot + W < S) ? W : warp + S - slot;
             if (i + d >= cnt) break;
@@ -656,14 +688,17 @@ struct FusedArgs {
                                   // every block's phase ends of iteration 2 (8 x grid, after 128)
     int leave_early;              // failure-detection test: block 0 leaves before its first grid barrier
     int trace0;                   // first ring sequence number of block 0's chunk trace (see Ring)
+    int qcache;                   // 1: q (and P_H's z) cached in shared memory between passes;
+                                  // 0: recomputed from global memory (same arithmetic), which
+                                  // leaves room for the ring when m2-vectors of TO are large
 };
 
-// Shared-memory layout of the persistent kernel: staged vector, three m2-vector
-// caches (q or z, r, p in TO), the per-row chunk partials, then the ring (slots,
-// full and empty mbarriers, last-fill words, stop flag).
+// Shared-memory layout of the persistent kernel: staged vector, the m2-vector
+// caches (r, p, and with qcache q or z, in TO), the per-row chunk partials, then
+// the ring (slots, full and empty mbarriers, last-fill words, stop flag).
 template <typename TO>
-inline size_t fused_spart_offset(size_t xs_bytes, int m2) {
-    const size_t o = xs_bytes + 3 * (size_t)m2 * sizeof(TO);
+inline size_t fused_spart_offset(size_t xs_bytes, int m2, int qcache) {
+    const size_t o = xs_bytes + (size_t)(2 + (qcache ? 1 : 0)) * (size_t)m2 * sizeof(TO);
     return (o + 15) / 16 * 16;
 }
 inline size_t fused_ring_offset(size_t spart_off, size_t spart_bytes) {
@@ -705,9 +740,10 @@ __global__ void __launch_bounds__(NT, NT == kSmallBlock ? 2 : 1)
     extern __shared__ __align__(128) unsigned char pcg_smem[];
     TO* xs = reinterpret_cast<TO*>(pcg_smem);
     TP* xp = reinterpret_cast<TP*>(pcg_smem);
-    TO* qc = reinterpret_cast<TO*>(pcg_smem + a.xs_bytes);
-    TO* rc = qc + a.m2;
+    TO* rc = reinterpret_cast<TO*>(pcg_smem + a.xs_bytes);
     TO* pcs = rc + a.m2;
+    TO* qc = pcs + a.m2;             // (only with a.qcache)
+    const bool qcache = a.qcache != 0;
     Ring R;
     R.S = a.slots;
     R.slot_bytes = a.slot_bytes;
@@ -823,8 +859,8 @@ __global__ void __launch_bounds__(NT, NT == kSmallBlock ? 2 : 1)
         // Each thread takes the elements j = tid + u T, all of a pass's global loads issued
         // before any is used (one round of latency per pass); sums in increasing u.
         AT pq = AT(0);
+        const TO* w = a.out[a.nop - 1];
         {
-            const TO* w = a.out[a.nop - 1];
             TO wv[kNU], dv[kNU];
 #pragma unroll
             for (int u = 0; u < kNU; ++u) {
@@ -837,13 +873,13 @@ __global__ void __launch_bounds__(NT, NT == kSmallBlock ? 2 : 1)
                 const int j = tid + u * T;
                 if (j < m2) {
                     const TO q = (TO)fma((AT)dv[u], (AT)pcs[j], (AT)wv[u]);
-                    qc[j] = q;
+                    if (qcache) qc[j] = q;
                     pq = fma((AT)pcs[j], (AT)q, pq);
                 }
             }
             for (int j = tid + kNU * T; j < m2; j += T) {
                 const TO q = (TO)fma((AT)__ldg(a.D + j), (AT)pcs[j], (AT)__ldcg(w + j));
-                qc[j] = q;
+                if (qcache) qc[j] = q;
                 pq = fma((AT)pcs[j], (AT)q, pq);
             }
         }
@@ -866,7 +902,8 @@ __global__ void __launch_bounds__(NT, NT == kSmallBlock ? 2 : 1)
                 gv[u] = (PC == PC_H_K && j < m2) ? __ldg(a.sg + j) : TP(0);
             }
             auto update = [&](int j, TO dzj, TP sgj) {
-                const TO rn = fma(-al, qc[j], rc[j]);
+                const TO qj = qcache ? qc[j] : (TO)fma((AT)__ldg(a.D + j), (AT)pcs[j], (AT)__ldcg(w + j));
+                const TO rn = fma(-al, qj, rc[j]);
                 rc[j] = rn;
                 rrp = fma((AT)rn, (AT)rn, rrp);
                 if (j >= own0 && j < own1) xo[j - own0] = fma(al, pcs[j], xo[j - own0]);
@@ -903,6 +940,7 @@ __global__ void __launch_bounds__(NT, NT == kSmallBlock ? 2 : 1)
         if (it >= maxit) { done = 2; break; }
 
         AT rz_new;
+        const TP* vout = a.outP[a.npc > 0 ? a.npc - 1 : 0];
         if (PC == PC_H_K) {
             // ---- (a9) v = P~^{-1} (Sg r) (one symmetric phase, or W then W'), z = Sg v
             for (int k = 0; k < a.npc; ++k) {
@@ -919,7 +957,6 @@ __global__ void __launch_bounds__(NT, NT == kSmallBlock ? 2 : 1)
                 if (!gsync()) { leave(); return; }
             }
             mark(it - 1, 8);
-            const TP* vout = a.outP[a.npc - 1];
             // z into the q cache (q is no longer needed), then r'z
             rzp = AT(0);
             {
@@ -935,13 +972,13 @@ __global__ void __launch_bounds__(NT, NT == kSmallBlock ? 2 : 1)
                     const int j = tid + u * T;
                     if (j < m2) {
                         const TO z = (TO)((ATP)sv[u] * (ATP)vv[u]);
-                        qc[j] = z;
+                        if (qcache) qc[j] = z;
                         rzp = fma((AT)rc[j], (AT)z, rzp);
                     }
                 }
                 for (int j = tid + kNU * T; j < m2; j += T) {
                     const TO z = (TO)((ATP)__ldg(a.sg + j) * (ATP)__ldcg(vout + j));
-                    qc[j] = z;
+                    if (qcache) qc[j] = z;
                     rzp = fma((AT)rc[j], (AT)z, rzp);
                 }
             }
@@ -957,7 +994,9 @@ __global__ void __launch_bounds__(NT, NT == kSmallBlock ? 2 : 1)
         for (int j = tid; j < padO_m2; j += T) {
             TO v = TO(0);
             if (j < m2) {
-                const TO z = (PC == PC_H_K) ? qc[j] : xs[j];
+                TO z;
+                if (PC == PC_H_K) z = qcache ? qc[j] : (TO)((ATP)__ldg(a.sg + j) * (ATP)__ldcg(vout + j));
+                else z = xs[j];
                 v = fma(be, pcs[j], z);
                 pcs[j] = v;
             }
