@@ -1925,6 +1925,7 @@ public:
             return newton_solve(ox, ol, on);
         }
         if (paper) return QP_OK;
+        long long iters32 = use64 ? 0 : it;   // this direction's PCG iterations with the FP32 operator
         double prev = kkt3_residual(ox, ol, on);
         const double rtol2 = opt.refine_tol * opt.refine_tol * fnorm2;
         if (verbose) std::fprintf(stderr, "      refine 0: |rho|/|f|=%.3e\n", std::sqrt(prev / fnorm2));
@@ -1945,6 +1946,7 @@ public:
             last = prev;
             it = reduced_solve(rho_g, rho_e, rho_a, tx, tl, tn, kind, ctol, maxit, std::sqrt(prev));
             if (it < 0) return QP_ENUMERIC;
+            if (!use64) iters32 += it;
             axpby<double, double>(n, 1.0, tx, 1.0, ox, s);
             if (m1) axpby<double, double>(m1, 1.0, tl, 1.0, ol, s);
             axpby<double, double>(m2, 1.0, tn, 1.0, on, s);
@@ -1966,8 +1968,23 @@ public:
             }
             prev = r2;
         }
+        // Corollaries 1 and 2 bound CG by n - m1 + 1 (P_L) or m1 + 1 (P_H) iterations in
+        // exact arithmetic.  Far beyond that, rounding drives the count (late in the IPM
+        // P_L's spectrum grows without bound, Theorem 1), and FP32 CG needs several times
+        // the FP64 iterations per direction -- more than its cheaper iterations repay:
+        // the QP's later directions use the FP64 operator.
+        const long long bound = (kind == PC_L_K) ? (long long)(n - m1 + 1) : (kind == PC_H_K) ? (long long)(m1 + 1) : m2;
+        if (!use64 && allow_pc64 && opt.pcg_tol <= 0 && iters32 > kCgExcess * bound) {
+            if (verbose) std::fprintf(stderr, "  %lld FP32 PCG iterations for one direction (bound %lld)\n", iters32, bound);
+            switch_to_op64();
+        }
         return QP_OK;
     }
+    // FP32 CG iterations per direction, in units of the exact-arithmetic bound, beyond
+    // which the mixed path moves to the FP64 operator (n=3000 few-dof workload: from
+    // IPM iteration 14 on, where an FP32 direction took about 20,000 iterations against
+    // 7,000 in FP64 at three times the cost per iteration).
+    static constexpr long long kCgExcess = 32;
 
     // -------------------------------------------------------------------- IPM
     // |r_g|_inf, |r_e|_inf, |r_i|_inf, s'nu, x'Hx, c'x at the current iterate.

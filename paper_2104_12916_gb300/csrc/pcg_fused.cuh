@@ -501,6 +501,7 @@ __device__ __forceinline__ void consume_phase(const Phase& ph, const BlockRange 
                         const int xo = (int)((e0 - rl * ld) / VN);
                         TM a0 = TM(0), a1 = TM(0);
                         int v = v0 + lane;
+#pragma unroll 2
                         for (; v + 32 < v1; v += 64) {
                             a0 = VT::dot(sv[v], xv[xo + v], a0);
                             a1 = VT::dot(sv[v + 32], xv[xo + v + 32], a1);
