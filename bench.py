@@ -529,10 +529,17 @@ def batch_measure(B, local, qps, concurrency, pcg_form=-1, check_n=160, precs=No
          "e2e": {"value": round(sum(m["ok"]) / m["e2e_s"], 3), "unit": "QPs/s",
                  "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": sum(8 * q.n for q in qps)},
          "gpu_launches": int(m["launches"]), "clocks": m["clocks"]}
+    def failed(mm):
+        return [{"qp": i, "status": r["status"], "n": qps[i].n, "m1": qps[i].m1, "m2": qps[i].m2}
+                for i, r in enumerate(mm["res"]) if r["status"] != 0]
+    if failed(m):
+        d["failed"] = failed(m)
     if len(precs) > 1:
         m64 = out[precs[1]]
         d["fp64"] = {"value": round(sum(m64["ok"]) / m64["solve_s"], 3), "unit": "QPs/s",
                      "solved": f"{sum(m64['ok'])}/{len(qps)}"}
+        if failed(m64):
+            d["fp64"]["failed"] = failed(m64)
     return d
 
 

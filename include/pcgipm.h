@@ -145,6 +145,12 @@ typedef struct {
                              FP64 on the CUDA cores and rounded once (an FP32-accurate factor carries
                              about cond(H) u32 of relative error into H^{-1}; GB300 has no FP64
                              tensor path at useful rates). */
+    int autotune;         /* 1 (default): a QP whose persistent PCG kernel spans more than one
+                             thread-block cluster times a dozen iterations on a few grid sizes
+                             (the rule's, 3/4 and 1/2 of it, one block per SM) before its first
+                             solve in each precision and preconditioner, and keeps the fastest;
+                             results do not depend on the grid (fixed-order reductions), only
+                             the time does.  0: the rule of pcg_blocks alone. */
     void *stream;         /* cudaStream_t, or NULL for a library-created stream */
 } qp_opts;
 
@@ -166,6 +172,7 @@ typedef struct {
     int pc_switch_iter;   /* QP_PC_AUTO: IPM iteration of the switch from P_L to P_H, or -1 */
     int factor_tc;        /* 1 if the FP32 K0 factor was formed on the tensor cores (qp_opts.factor_tc) */
     int pcg_form_used;    /* the handle's pcg_form (QP_FORM_AUTO resolved at qp_create) */
+    int pcg_grid;         /* blocks of the last persistent PCG launch (after autotuning) */
 } qp_stats;
 
 /* Fill *opts with the defaults listed in the struct comments. */

@@ -143,6 +143,8 @@ struct Op {
     const TO *cval = nullptr, *ctval = nullptr;   // CSR values of C and C' (QPs created with a CSR C)
     TO *oU = nullptr, *oY, *oZ, *oW;   // persistent kernel: outputs of the operator phases
     TO *px = nullptr, *pr, *pz, *pp, *pq, *pu, *pz1, *pz2, *pt, *py, *prhs, *pD, *pDinv;
+    TO* zb = nullptr;          // persistent kernel, sliced FP64 update: z
+    double* segp = nullptr;    // persistent kernel, sliced FP64 update: per-segment partial sums
     TO *ku, *kw, *ke, *kz1, *kz2, *kt, *ka, *kmb, *wa, *wg;
     cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
     int graph_k[3] = {0, 0, 0};
@@ -535,6 +537,10 @@ public:
         o.px = vec<TO>(m2); o.pr = vec<TO>(m2); o.pz = vec<TO>(m2); o.pp = vec<TO>(m2); o.pq = vec<TO>(m2);
         o.pu = vec<TO>(n); o.pz1 = vec<TO>(n); o.pz2 = vec<TO>(m1); o.pt = vec<TO>(n); o.py = vec<TO>(n);
         o.prhs = vec<TO>(m2); o.pD = vec<TO>(m2); o.pDinv = vec<TO>(m2);
+        if (std::is_same<TO, double>::value) {
+            o.zb = vec<TO>(m2);
+            o.segp = vec<double>(2 * ((m2 + kSeg - 1) / kSeg));
+        }
         o.ku = vec<TO>(n); o.kw = vec<TO>(m1); o.ke = vec<TO>(m1); o.kz1 = vec<TO>(n); o.kz2 = vec<TO>(m1);
         o.kt = vec<TO>(n); o.ka = vec<TO>(n); o.kmb = vec<TO>(m1); o.wa = vec<TO>(m2); o.wg = vec<TO>(n);
         o.oU = vec<TO>(n); o.oY = vec<TO>(n); o.oZ = vec<TO>(n + m1); o.oW = vec<TO>(m2);
@@ -1264,7 +1270,11 @@ public:
         // the first phase's input is p (m2, padded); the P_H phases' is Sg r
         F.xs_elems_o = p32(m2);
         F.xs_elems_p = p32(m2);
-        F.xo_bytes = ((size_t)(m2 + grid - 1) / grid * sizeof(TO) + 15) / 16 * 16;
+        {   // the block's slice of x: m2 / grid elements, or whole kSeg segments (sliced FP64 update)
+            const size_t nseg = (size_t)(m2 + kSeg - 1) / kSeg;
+            const size_t el = std::max<size_t>((size_t)(m2 + grid - 1) / grid, (nseg + grid - 1) / grid * kSeg);
+            F.xo_bytes = (el * sizeof(TO) + 15) / 16 * 16;
+        }
         F.tbl.assign((size_t)(F.nop + F.npc) * (grid + 1), int2{0, 0});
         for (int k = 0; k < F.nop + F.npc; ++k) {
             Phase& ph = F.ph[k];
@@ -1351,7 +1361,8 @@ public:
         int dev = 0, sms = 0;
         PCG_CK(cudaGetDevice(&dev));
         PCG_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        const int grid = fused_grid(sms);
+        const int grid = grid_for<TO>(sms, PC);
+        stats.pcg_grid = grid;
         if (grid <= kMaxClusterBlocks) launch_fused_nt<TO, TP, PC, kSmallBlock>(grid, sms);
         else launch_fused_nt<TO, TP, PC, kBigBlock>(grid, sms);
     }
@@ -1385,6 +1396,7 @@ public:
         fa.D = o.pD; fa.Dinv = o.pDinv; fa.x = o.px;
         fa.r_in = o.pr; fa.p_in = o.pp;
         fa.st = st; fa.bar = bar;
+        fa.segp = o.segp; fa.zbuf = o.zb; fa.nseg = (m2 + kSeg - 1) / kSeg;
         fa.tstamp = phase_times ? tstamp : nullptr;
         fa.leave_early = leave_early ? 1 : 0;
         {   // block 0's chunks of iteration 2 (its items per iteration from the table)
@@ -1544,7 +1556,7 @@ public:
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const int grid = fused_grid(sms);
+        const int grid = grid_for<TO>(sms, kind);
         const FusedPlan F = plan_fused<TO, TP>(kind, grid);
         return fused_qcache<TO, TP>(F, grid) >= 0;
     }
@@ -1565,6 +1577,62 @@ public:
     }
 
     bool use_fused() const { return opt.pcg_check_every >= 0; }
+
+    // ---------------------------------------------------------------- autotuner
+    // Grid of the persistent kernel per operator precision and preconditioner kind:
+    // the tuned value once autotune_grid has run, else the rule (fused_grid).
+    int tuned_grid[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    int force_grid = 0;   // set while the autotuner times a candidate
+    template <typename TO>
+    int grid_for(int sms, int kind) const {
+        if (force_grid > 0) return force_grid;
+        const int t = tuned_grid[std::is_same<TO, double>::value ? 1 : 0][kind];
+        return t > 0 ? t : fused_grid(sms);
+    }
+    // Times a dozen PCG iterations (tolerance 0, the current right-hand side) for each
+    // candidate grid -- the rule's G, 3G/4, G/2 and one block per SM, every one larger
+    // than a cluster and with a ring that fits -- and keeps the fastest.  Only QPs whose
+    // rule grid exceeds a cluster are tuned (small QPs share the GPU by design); the grid
+    // never changes results, since every reduction has a grid-independent order.
+    template <typename TO, typename TP>
+    void autotune_grid(int kind) {
+        const int pk = std::is_same<TO, double>::value ? 1 : 0;
+        if (!opt.autotune || opt.pcg_blocks > 0 || !use_fused() || tuned_grid[pk][kind] != 0) return;
+        int dev = 0, sms = 0;
+        PCG_CK(cudaGetDevice(&dev));
+        PCG_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        const int g0 = fused_grid(sms);
+        tuned_grid[pk][kind] = g0;
+        if (g0 <= kMaxClusterBlocks) return;
+        std::vector<int> cand = {g0, std::max(kMaxClusterBlocks + 1, 3 * g0 / 4),
+                                 std::max(kMaxClusterBlocks + 1, g0 / 2), sms};
+        std::sort(cand.begin(), cand.end());
+        cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+        Op<TO>& o = op<TO>();
+        double best = 1e30;
+        int best_g = g0;
+        for (int g : cand) {
+            if (g > sms) continue;
+            force_grid = g;
+            const bool fits = fused_qcache<TO, TP>(plan_fused<TO, TP>(kind, g), g) >= 0;
+            if (!fits) continue;
+            double ms_best = 1e30;
+            for (int rep = 0; rep < 2; ++rep) {    // the first launch also uploads the tables
+                pcg_init<TO, TP>(kind, o.prhs, 0.0, 12, 0);
+                PCG_CK(cudaEventRecord(evA, s));
+                pcg_run_fused<TO, TP>(kind);
+                PCG_CK(cudaEventRecord(evB, s));
+                sync_check();
+                float ms = 0.f;
+                PCG_CK(cudaEventElapsedTime(&ms, evA, evB));
+                if (hst[0].iter > 0) ms_best = std::min(ms_best, (double)ms / hst[0].iter);
+            }
+            if (verbose) std::fprintf(stderr, "  autotune: grid %d, %.2f us per PCG iteration\n", g, ms_best * 1e3);
+            if (ms_best < best) { best = ms_best; best_g = g; }
+        }
+        force_grid = 0;
+        tuned_grid[pk][kind] = best_g;
+    }
 
     // CTAs of the persistent kernel.  A QP streaming at most 32 x 512 KB per iteration
     // gets between 8 and kMaxClusterBlocks (one cluster, about one per 512 KB), so
@@ -1667,6 +1735,7 @@ public:
     int pcg_solve_t(const double* rhs, double* dnu, int kind, double tol, int maxit, int* iters, double* relres) {
         Op<TO>& o = op<TO>();
         convert1d<double, TO>(m2, rhs, 1.0, o.prhs, s);
+        autotune_grid<TO, TP>(kind);
         pcg_init<TO, TP>(kind, o.prhs, tol, maxit, 0);
         pcg_run<TO, TP>(kind, maxit);
         convert1d<TO, double>(m2, o.px, 1.0, dnu, s);
@@ -1691,6 +1760,7 @@ public:
     template <typename TO, typename TP>
     void time_pcg_t(int kind, int warmup, int iters, double* ms_out) {
         Op<TO>& o = op<TO>();
+        autotune_grid<TO, TP>(kind);
         if (use_fused() && fused_fits<TO, TP>(kind)) {
             // warm-up solve, then a timed solve of `iters` iterations (tolerance 0:
             // no early stop); the timed region includes the start kernels.

@@ -66,6 +66,7 @@ constexpr int kMaxPhases = 6;                     // operator phases (pcg_form 2
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s bound on any wait
 constexpr unsigned kBarErr = 0x40000000u;         // error bit of the barrier counter
 constexpr int kNU = 16;                           // m2-vector elements per thread held in registers
+constexpr int kSeg = 64;                          // sliced FP64 update: elements per partial sum
 
 // Grid barrier word: a monotonic arrival counter (zeroed before each launch)
 // whose bit 30 records a failure anywhere, so one acquire load tells a polling
@@ -689,6 +690,9 @@ struct FusedArgs {
                                   // every block's phase ends of iteration 2 (8 x grid, after 128)
     int leave_early;              // failure-detection test: block 0 leaves before its first grid barrier
     int trace0;                   // first ring sequence number of block 0's chunk trace (see Ring)
+    double* segp;                 // sliced FP64 update: per-segment partials of r'r (first nseg) and r'z
+    TO* zbuf;                     // sliced FP64 update: z = P_L^{-1} r, every block's slice
+    int nseg;                     // ceil(m2 / kSeg)
     int qcache;                   // 1: q (and P_H's z) cached in shared memory between passes;
                                   // 0: recomputed from global memory (same arithmetic), which
                                   // leaves room for the ring when m2-vectors of TO are large
@@ -790,10 +794,22 @@ __global__ void __launch_bounds__(NT, NT == kSmallBlock ? 2 : 1)
     TP* spartP = reinterpret_cast<TP*>(pcg_smem + a.spart_off);
     // slice of x this block owns: accumulated in shared memory (x = 0 at entry),
     // written to global memory when the solve ends
+    // With an FP64 operator and P_L (or no preconditioner) the r, x and z updates are
+    // sliced: block b updates only the elements of segments [sb, se) (kSeg elements
+    // each), publishes z and the segments' partial sums of r'r and r'z, and after one
+    // more grid barrier every block adds the partials in segment order.  The update's
+    // 5 FP64 operations per element then run once on the GPU instead of once per block
+    // (the FP64 pipe issues 2 per clock per SM), and every sum keeps an order that does
+    // not depend on the grid.
+    constexpr bool SL = std::is_same<TO, double>::value && PC != PC_H_K;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int sb = (int)((long long)a.nseg * blockIdx.x / nblocks);
+    const int se = (int)((long long)a.nseg * (blockIdx.x + 1) / nblocks);
     const int per = (m2 + nblocks - 1) / nblocks;
-    const int own0 = blockIdx.x * per, own1 = min(m2, own0 + per);
+    const int own0 = SL ? min(m2, sb * kSeg) : (int)blockIdx.x * per;
+    const int own1 = SL ? min(m2, se * kSeg) : min(m2, own0 + per);
     TO* xo = reinterpret_cast<TO*>(pcg_smem + a.xo_off);
-    for (int j = tid; j < per; j += T) xo[j] = TO(0);
+    for (int j = tid; j < own1 - own0; j += T) xo[j] = TO(0);
     // staged m2-vectors are padded to 32 elements (the leading dimension of C' and P~^{-1})
     const int padO_m2 = ((m2 + 31) / 32) * 32, padP_m2 = padO_m2;
     const bool stamp = a.tstamp != nullptr && blockIdx.x == 0 && tid == 0;
@@ -891,7 +907,47 @@ __global__ void __launch_bounds__(NT, NT == kSmallBlock ? 2 : 1)
         const AT alpha = rz / pq;
         const TO al = (TO)alpha;
         AT rrp = AT(0), rzp = AT(0);
-        {
+        if (SL) {
+            // this block's segments: one warp per segment, lanes on elements k * 32 + lane
+            for (int sg = sb + warp; sg < se; sg += Blk<NT>::warps) {
+                AT prr = AT(0), prz = AT(0);
+#pragma unroll
+                for (int k = 0; k < kSeg / 32; ++k) {
+                    const int j = sg * kSeg + k * 32 + lane;
+                    if (j < m2) {
+                        const TO qj = qcache ? qc[j] : (TO)fma((AT)__ldg(a.D + j), (AT)pcs[j], (AT)__ldcg(w + j));
+                        const TO rn = fma(-al, qj, rc[j]);
+                        rc[j] = rn;
+                        prr = fma((AT)rn, (AT)rn, prr);
+                        xo[j - own0] = fma(al, pcs[j], xo[j - own0]);
+                        const TO z = (PC == PC_L_K) ? rn * __ldg(a.Dinv + j) : rn;
+                        a.zbuf[j] = z;
+                        prz = fma((AT)rn, (AT)z, prz);
+                    }
+                }
+                prr = warp_sum(prr);
+                prz = warp_sum(prz);
+                if (lane == 0) {
+                    a.segp[sg] = (double)prr;
+                    a.segp[a.nseg + sg] = (double)prz;
+                }
+            }
+            if (!gsync()) { leave(); return; }
+            if (warp == 0) {
+                AT srr = AT(0), srz = AT(0);
+                for (int sg = lane; sg < a.nseg; sg += 32) {
+                    srr += (AT)__ldcg(a.segp + sg);
+                    srz += (AT)__ldcg(a.segp + a.nseg + sg);
+                }
+                srr = warp_sum(srr);
+                srz = warp_sum(srz);
+                if (lane == 0) { sh[32] = srr; sh[33] = srz; }
+            }
+            csync<NT>();
+            rrp = sh[32];
+            rzp = sh[33];
+            csync<NT>();
+        } else {
             // the preconditioner's diagonal factor: 1/D (P_L) or the Jacobi scaling Sg (P_H)
             const TO* dz = (PC == PC_L_K) ? a.Dinv : nullptr;
             TO zv[kNU];
@@ -927,7 +983,9 @@ __global__ void __launch_bounds__(NT, NT == kSmallBlock ? 2 : 1)
         for (int j = m2 + tid; j < padO_m2; j += T) {
             if (PC == PC_H_K) xp[j] = TP(0); else xs[j] = TO(0);
         }
-        if (PC == PC_H_K) {
+        if (SL) {
+            rr = rrp;
+        } else if (PC == PC_H_K) {
             rr = block_allsum<NT>(rrp, sh);
         } else {
             block_allsum2<NT>(rrp, rzp, sh);
@@ -997,7 +1055,7 @@ __global__ void __launch_bounds__(NT, NT == kSmallBlock ? 2 : 1)
             if (j < m2) {
                 TO z;
                 if (PC == PC_H_K) z = qcache ? qc[j] : (TO)((ATP)__ldg(a.sg + j) * (ATP)__ldcg(vout + j));
-                else z = xs[j];
+                else z = SL ? __ldcg(a.zbuf + j) : xs[j];
                 v = fma(be, pcs[j], z);
                 pcs[j] = v;
             }

@@ -82,6 +82,7 @@ void qp_opts_default(qp_opts* o) {
     o->blocking_wait = 0;
     o->pcg_form = QP_FORM_AUTO;
     o->factor_tc = 0;
+    o->autotune = 1;
     o->stream = nullptr;
 }
 

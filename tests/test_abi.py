@@ -46,7 +46,7 @@ def test_host_only_calls(lib):
 def test_new_option_defaults(lib):
     o = binding.qp_opts_default()
     assert o.pcg_blocks == 0 and o.blocking_wait == 0 and o.mixed_fallback == 1
-    assert o.pcg_form == binding.QP_FORM_AUTO and o.factor_tc == 0
+    assert o.pcg_form == binding.QP_FORM_AUTO and o.factor_tc == 0 and o.autotune == 1
     assert o.precond == binding.QP_PC_AUTO and o.pcg_mode == binding.QP_MODE_PARITY
 
 
