@@ -151,3 +151,29 @@ def test_server_rejects_what_can_never_fit(B):
     with pytest.raises(B.QPError) as e:
         srv.poll(12345)
     srv.close()
+
+
+@pytest.mark.parametrize("prec", [1, 0])
+def test_server_large_requests_match_oracle(B, prec):
+    """Requests of the served workload itself with n > 1024 (requests 54, 19 and 89
+    of its stream: P_H with few and with more equalities, and P_L with few degrees
+    of freedom), served among small ones: each result equals the same QP solved
+    alone and the FP64 oracle's optimum."""
+    big = [qpgen.serving_qp(i) for i in (54, 19, 89)]
+    assert all(q.n > 1024 for q in big)
+    qps = big + _requests(4, seed0=900)
+    o = B.qp_opts_default()
+    o.precision = prec
+    srv = B.Server(budget_bytes=sum(B.qp_device_bytes_bound(q.n, q.m1, q.m2, o) for q in qps),
+                   max_slots=4, opts=o)
+    tickets = [srv.submit(q) for q in qps]
+    assert srv.drain(timeout_ms=600_000) == B.QP_OK
+    got = [srv.poll(t) for t in tickets]
+    srv.close()
+    for q, (res, x) in zip(big, got[:len(big)]):
+        assert res["status"] == B.QP_OK, (q.name, res)
+        st_a, f_a, its_a, x_a = _solve_alone(B, q, o)
+        assert st_a == B.QP_OK and np.array_equal(x, x_a) and res["obj"] == f_a, q.name
+        ref = ipm.solve_qp(q, variant="kkt3")
+        assert abs(res["obj"] - ref.f) / max(abs(ref.f), 1.0) <= 1e-6, (q.name, res["obj"], ref.f)
+        assert abs(res["ipm_iters"] - ref.iters) <= 2, (q.name, res["ipm_iters"], ref.iters)
