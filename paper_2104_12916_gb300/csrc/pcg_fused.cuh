@@ -877,6 +877,13 @@ __global__ void __launch_bounds__(NT, NT == kSmallBlock ? 2 : 1)
         // before any is used (one round of latency per pass); sums in increasing u.
         AT pq = AT(0);
         const TO* w = a.out[a.nop - 1];
+        // the next pass's 1/D (P_L), loaded here so that its latency overlaps this pass
+        TO zv[kNU];
+#pragma unroll
+        for (int u = 0; u < kNU; ++u) {
+            const int j = tid + u * T;
+            zv[u] = (PC == PC_L_K && j < m2) ? __ldg(a.Dinv + j) : TO(1);
+        }
         {
             TO wv[kNU], dv[kNU];
 #pragma unroll
@@ -950,12 +957,10 @@ __global__ void __launch_bounds__(NT, NT == kSmallBlock ? 2 : 1)
         } else {
             // the preconditioner's diagonal factor: 1/D (P_L) or the Jacobi scaling Sg (P_H)
             const TO* dz = (PC == PC_L_K) ? a.Dinv : nullptr;
-            TO zv[kNU];
             TP gv[kNU];
 #pragma unroll
             for (int u = 0; u < kNU; ++u) {
                 const int j = tid + u * T;
-                zv[u] = (PC == PC_L_K && j < m2) ? __ldg(dz + j) : TO(1);
                 gv[u] = (PC == PC_H_K && j < m2) ? __ldg(a.sg + j) : TP(0);
             }
             auto update = [&](int j, TO dzj, TP sgj) {
