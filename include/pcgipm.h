@@ -151,6 +151,13 @@ typedef struct {
                              solve in each precision and preconditioner, and keeps the fastest;
                              results do not depend on the grid (fixed-order reductions), only
                              the time does.  0: the rule of pcg_blocks alone. */
+    int factor_bk;        /* 1: also factor K0 = [H A'; A 0] as P K0 P' = L D L' with Bunch-Kaufman
+                             partial pivoting (the paper's setup factorization, Sec. 6: SYTRF) on the
+                             GPU, check its inertia against (n, m1) (Sec. 4.1; QP_ENOTCONVEX
+                             otherwise, QP_ESINGULAR for a zero column) and form M0 = [K0^{-1}]_11
+                             = Z' D^{-1} Z, Z = L^{-1} P [I_n; 0], from it (pcg_form 0 and 3); the
+                             other K0 solves keep the structured factor.  0 (default): M0 from the
+                             structured factor R^{-1} R^{-T} - Et' Et. */
     void *stream;         /* cudaStream_t, or NULL for a library-created stream */
 } qp_opts;
 
@@ -173,6 +180,9 @@ typedef struct {
     int factor_tc;        /* 1 if the FP32 K0 factor was formed on the tensor cores (qp_opts.factor_tc) */
     int pcg_form_used;    /* the handle's pcg_form (QP_FORM_AUTO resolved at qp_create) */
     int pcg_grid;         /* blocks of the last persistent PCG launch (after autotuning) */
+    int k0_inertia_pos;   /* qp_opts.factor_bk: positive, negative eigenvalues of D (K0's inertia), */
+    int k0_inertia_neg;   /*   and the number of 2x2 pivots; -1 without factor_bk */
+    int k0_pivots_2x2;
 } qp_stats;
 
 /* Fill *opts with the defaults listed in the struct comments. */

@@ -39,7 +39,7 @@ class qp_opts(ct.Structure):
         ("pcg_tol", ct.c_double), ("refine_tol", ct.c_double), ("tol_feas", ct.c_double),
         ("tol_mu", ct.c_double), ("pcg_check_every", ct.c_int), ("mixed_fallback", ct.c_int),
         ("pcg_blocks", ct.c_int), ("blocking_wait", ct.c_int), ("pcg_form", ct.c_int),
-        ("factor_tc", ct.c_int), ("autotune", ct.c_int), ("stream", ct.c_void_p),
+        ("factor_tc", ct.c_int), ("autotune", ct.c_int), ("factor_bk", ct.c_int), ("stream", ct.c_void_p),
     ]
 
 
@@ -83,7 +83,8 @@ class qp_stats(ct.Structure):
         ("t_precond_ms", ct.c_double), ("op64_solves", ct.c_int), ("op64_switch_iter", ct.c_int),
         ("pc64_switch_iter", ct.c_int),
         ("pc_switch_iter", ct.c_int), ("factor_tc", ct.c_int), ("pcg_form_used", ct.c_int),
-        ("pcg_grid", ct.c_int),
+        ("pcg_grid", ct.c_int), ("k0_inertia_pos", ct.c_int), ("k0_inertia_neg", ct.c_int),
+        ("k0_pivots_2x2", ct.c_int),
     ]
 
     def as_dict(self):

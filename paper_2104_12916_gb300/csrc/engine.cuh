@@ -26,6 +26,7 @@
 #include "../../include/pcgipm.h"
 #include "common.cuh"
 #include "dense.cuh"
+#include "dense_bk.cuh"
 #include "gemv.cuh"
 #include "pcg_fused.cuh"
 #include "vec.cuh"
@@ -233,6 +234,7 @@ public:
         form_auto = (opt.pcg_form == QP_FORM_AUTO);
         opt.pcg_form = resolve_form(opt.pcg_form, n, m1, m2, csr_c);
         stats.pcg_form_used = opt.pcg_form;
+        stats.k0_inertia_pos = stats.k0_inertia_neg = stats.k0_pivots_2x2 = -1;
         f64 = (opt.precision == QP_PREC_FP64);
         use64 = f64;
         pc64 = f64;
@@ -335,6 +337,8 @@ public:
         const bool ph = o.precond != QP_PC_PL && o.precond != QP_PC_NONE;
         b += (size_t)kMaxPhases * kTblStride * 8 + 256 + (128 + 8 * 1024) * 8 + 256;
         b += op(8, false);                       // the factor is formed in FP64
+        if (o.factor_bk && (o.pcg_form == 0 || o.pcg_form == 3))   // K0 in full, Z and D^{-1} Z, pivot data
+            b += mat(n + m1, n + m1, 8) + 2 * mat(n + m1, n, 8) + 8 * v(n + m1, 8) + 8 * v(2048, 8);
         if (fp32) {
             b += op(4, true);
             if (ph) b += pc(4) + (o.mixed_fallback ? pc(8) : 0);
@@ -564,6 +568,104 @@ public:
     }
 
     bool fp32_pivot_warn = false;
+
+    // Bunch-Kaufman LDL' of K0 (qp_opts.factor_bk): inertia check and M0 = Z' D^{-1} Z.
+    void bk_m0(double* M0, long long ldm0) {
+        const int N = n + m1;
+        const long long ldk = pad_ld(N), ldz = pad_ld(n);
+        double *K = nullptr, *Z = nullptr, *Y = nullptr, *aux = nullptr;
+        auto galloc = [&](double** p, size_t count) {
+            if (cudaMallocAsync(p, count * sizeof(double) + 256, s) != cudaSuccess) {
+                cudaGetLastError();
+                if (K) cudaFreeAsync(K, s);
+                if (Z) cudaFreeAsync(Z, s);
+                if (Y) cudaFreeAsync(Y, s);
+                throw NoMem{};
+            }
+        };
+        galloc(&K, (size_t)N * ldk);
+        galloc(&Z, (size_t)N * ldz);
+        galloc(&Y, (size_t)N * ldz);
+        galloc(&aux, (size_t)6 * ldk + 4096 + 64);
+        double* w = aux;                                   // 2 N
+        double* d = aux + 2 * ldk;                         // N
+        double* e = aux + 3 * ldk;                         // N
+        int* perm = reinterpret_cast<int*>(aux + 4 * ldk);                 // N ints
+        int* ptype = reinterpret_cast<int*>(aux + 5 * ldk);                // N ints
+        double* cval = aux + 6 * ldk;                      // 2 x 1024
+        int* cidx = reinterpret_cast<int*>(cval + 2048);   // 2 x 1024 ints
+        unsigned* pbar = reinterpret_cast<unsigned*>(cidx + 2048);
+        int* perr = reinterpret_cast<int*>(pbar + 4);
+        int* pstat = perr + 1;
+        PCG_CK(cudaMemsetAsync(pbar, 0, 32, s));
+        bk_build_k0_kernel<<<vec_grid(N), kVecThreads, 0, s>>>(H.p, H.ld, A.p, A.ld, n, m1, K, ldk, perm);
+        int dev = 0, sms = 0;
+        PCG_CK(cudaGetDevice(&dev));
+        PCG_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        const int G = std::max(1, std::min(std::min(sms, 1024), N / 16));
+        BkArgs ba{K, ldk, N, w, cval, cidx, perm, d, e, ptype, pbar, perr, pstat};
+        void* args[] = {(void*)&ba};
+        PCG_CK(cudaLaunchCooperativeKernel((const void*)bk_factor_kernel, G, kBkThreads, args, 0, s));
+        std::vector<double> hd(N), he(N);
+        std::vector<int> ht(N);
+        int flags[2] = {0, 0};
+        PCG_CK(cudaMemcpyAsync(flags, perr, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        PCG_CK(cudaMemcpyAsync(hd.data(), d, N * sizeof(double), cudaMemcpyDeviceToHost, s));
+        PCG_CK(cudaMemcpyAsync(he.data(), e, N * sizeof(double), cudaMemcpyDeviceToHost, s));
+        PCG_CK(cudaMemcpyAsync(ht.data(), ptype, N * sizeof(int), cudaMemcpyDeviceToHost, s));
+        wait_stream();
+        PCG_CK(cudaGetLastError());
+        auto release = [&]() { cudaFreeAsync(K, s); cudaFreeAsync(Z, s); cudaFreeAsync(Y, s); cudaFreeAsync(aux, s); };
+        if (flags[0]) { release(); throw QpError{QP_ETIMEOUT}; }
+        if (flags[1]) { release(); throw QpError{QP_ESINGULAR}; }
+        // inertia of D (Sylvester): 1x1 blocks by sign; a 2x2 block with det < 0 has one of each
+        int pos = 0, neg = 0, two = 0;
+        for (int i = 0; i < N; ++i) {
+            if (ht[i] == 1) {
+                (hd[i] > 0 ? pos : neg) += 1;
+            } else if (ht[i] == 2) {
+                const double det = hd[i] * hd[i + 1] - he[i] * he[i];
+                ++two;
+                if (det < 0) { ++pos; ++neg; }
+                else if (hd[i] > 0) pos += 2;
+                else neg += 2;
+            }
+        }
+        stats.k0_inertia_pos = pos;
+        stats.k0_inertia_neg = neg;
+        stats.k0_pivots_2x2 = two;
+        if (pos != n || neg != m1) {
+            if (verbose) std::fprintf(stderr, "  K0 inertia (%d, %d), expected (%d, %d)\n", pos, neg, n, m1);
+            release();
+            throw QpError{QP_ENOTCONVEX};
+        }
+        // Z = L^{-1} P [I_n; 0] by 64-row blocks, Y = D^{-1} Z, M0 = Z' Y
+        const long long total = (long long)N * ldz;
+        bk_pe_kernel<<<(int)std::min<long long>((total + 255) / 256, 152LL * 16), 256, 0, s>>>(perm, N, n, Z, ldz);
+        for (int k0 = 0; k0 < N; k0 += kBkRows) {
+            const int kb = std::min(kBkRows, N - k0);
+            if (k0 > 0) {
+                GemmArgs<double> g{};
+                g.M = kb; g.N = n; g.K = k0;
+                g.A = K + (long long)k0 * ldk; g.sai = ldk; g.sak = 1;
+                g.B = Z; g.sbk = ldz; g.sbj = 1;
+                g.C = Z + (long long)k0 * ldz; g.ldc = ldz; g.alpha = -1.0; g.beta = 1.0;
+                gemm<double>(g, s);
+            }
+            bk_trsm_block_kernel<<<(n + 127) / 128, 128, 0, s>>>(K, ldk, k0, kb, Z, ldz, n);
+        }
+        bk_dinv_kernel<<<(int)std::min<long long>(((long long)N * n + 255) / 256, 152LL * 16), 256, 0, s>>>(
+            d, e, ptype, N, n, Z, Y, ldz);
+        GemmArgs<double> h{};
+        h.M = n; h.N = n; h.K = N;
+        h.A = Z; h.sai = 1; h.sak = ldz;
+        h.B = Y; h.sbk = ldz; h.sbj = 1;
+        h.C = M0; h.ldc = ldm0; h.alpha = 1.0; h.beta = 0.0;
+        gemm<double>(h, s);
+        release();
+        wait_stream();
+        PCG_CK(cudaGetLastError());
+    }
     bool form_auto = false;   // pcg_form was QP_FORM_AUTO
 
     // Scratch of the tensor-core products (TF32 hi/lo splits of their operands),
@@ -819,6 +921,7 @@ public:
                 gemm<TO>(h, s);
             }
         }
+        if (opt.factor_bk && o.M0.p && std::is_same<TO, double>::value) bk_m0(reinterpret_cast<double*>(o.M0.p), o.M0.ld);
         if (opt.pcg_form == 3 && o.lr > 0) {
             // M0 = Z Z' with Z (n x r), r = n - m1 (M0 = R^{-1} (I - P) R^{-T}, P the orthogonal
             // projector onto the row space of A R^{-1}, of rank m1): pivoted Cholesky, then

@@ -83,6 +83,7 @@ void qp_opts_default(qp_opts* o) {
     o->pcg_form = QP_FORM_AUTO;
     o->factor_tc = 0;
     o->autotune = 1;
+    o->factor_bk = 0;
     o->stream = nullptr;
 }
 

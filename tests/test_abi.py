@@ -46,7 +46,7 @@ def test_host_only_calls(lib):
 def test_new_option_defaults(lib):
     o = binding.qp_opts_default()
     assert o.pcg_blocks == 0 and o.blocking_wait == 0 and o.mixed_fallback == 1
-    assert o.pcg_form == binding.QP_FORM_AUTO and o.factor_tc == 0 and o.autotune == 1
+    assert o.pcg_form == binding.QP_FORM_AUTO and o.factor_tc == 0 and o.autotune == 1 and o.factor_bk == 0
     assert o.precond == binding.QP_PC_AUTO and o.pcg_mode == binding.QP_MODE_PARITY
 
 
@@ -70,6 +70,7 @@ def test_device_bytes_bound_host_logic(lib):
     assert pl < auto and pl >= fp64_copies                  # an explicit P_L never builds P_H
     assert _bound(n, m1, m2, mixed_fallback=0) < auto       # no FP64 operator or P_H to move to
     assert _bound(n, m1, m2, pcg_form=1) >= auto + 4 * 2 * (n + m1) * m2   # B and B' (FP32)
+    assert _bound(n, m1, m2, pcg_form=0, factor_bk=1) >= _bound(n, m1, m2, pcg_form=0) + 8 * (n + m1) ** 2
     f64 = _bound(n, m1, m2, precision=binding.QP_PREC_FP64)
     assert f64 >= fp64_copies + 8 * 4 * m2 * m2
     for dn, dm1, dm2 in ((50, 0, 0), (0, 20, 0), (0, 0, 100)):
