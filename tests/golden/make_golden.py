@@ -4,6 +4,7 @@ Calls only ``oracle`` and ``qpgen``.  The GPU tests compare against these
 files instead of re-running the slow CPU oracle on the large workloads.
 
     python tests/golden/make_golden.py 0 1 2
+    python tests/golden/make_golden.py many      # batched and served QPs (oracle_batch_serving.json)
 """
 import json
 import os
@@ -44,5 +45,26 @@ def main(configs):
         print(k, r.status, r.iters, r.f, f"{dt:.1f}s", flush=True)
 
 
+def many(batch_n=160, serve_n=256, serve_idx=400):
+    """Oracle optima of the batched workload's QPs with n <= batch_n (all 512) and of
+    the served stream's requests 0..serve_idx-1 with n <= serve_n, keyed by QP name:
+    the batch and serving measurements check their results against these."""
+    out = {"objective": {}, "ipm_iters": {}, "source": "oracle.ipm.solve_qp (kkt3) on qpgen.batch_qp(i), "
+           f"i < 512 with n <= {batch_n}, and qpgen.serving_qp(i), i < {serve_idx} with n <= {serve_n}"}
+    qps = [qpgen.batch_qp(i) for i in range(512) if qpgen.batch_dims(i)[0] <= batch_n]
+    qps += [qpgen.serving_qp(i) for i in range(serve_idx) if qpgen.serving_dims(i)[0] <= serve_n]
+    t0 = time.time()
+    for q in qps:
+        r = ipm.solve_qp(q, variant="kkt3")
+        out["objective"][q.name] = r.f
+        out["ipm_iters"][q.name] = r.iters
+    with open(os.path.join(HERE, "oracle_batch_serving.json"), "w") as fh:
+        json.dump(out, fh, indent=0)
+    print(len(qps), "QPs", f"{time.time() - t0:.1f}s", flush=True)
+
+
 if __name__ == "__main__":
-    main([int(a) for a in sys.argv[1:]] or [0])
+    if sys.argv[1:] == ["many"]:
+        many()
+    else:
+        main([int(a) for a in sys.argv[1:]] or [0])
